@@ -1,0 +1,217 @@
+/*
+ * lya.h -- C ABI of the GB300 Lyman-alpha pixel-pair library (liblya.so).
+ *
+ * The library computes, for a catalogue of Lyman-alpha forests, the binned
+ * two-point estimator of arxiv 2507.00129 Eq. (2.4)
+ *
+ *     xi_A = sum_{(i,j) in A} (w_i d_i)(w_j d_j) / sum_{(i,j) in A} w_i w_j ,
+ *
+ * its distortion matrix (Eq. 2.6, with the continuum projection eta of
+ * Eq. 2.7), the projection itself, and the gradient of xi with respect to the
+ * deltas and weights.  Pixel pairs (i, j) come from different forests
+ * (Section 2.1); a pair falls in bin A = p * n_perp + t when
+ *
+ *     p = floor(r_par / D_par),  t = floor(r_perp / D_perp),  p < n_par, t < n_perp,
+ *     r_par = |d_i - d_j| cos(theta/2),  r_perp = (d_i + d_j) sin(theta/2),
+ *
+ * with D = r_max / n and theta the angle between the two lines of sight.
+ * Every unordered forest pair is counted once.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller; the library
+ *    never frees or retains them past the call.  Scratch memory (pair lists,
+ *    packed pixels, accumulators) is owned by the handle, allocated on first
+ *    use, reused by later calls and released by lya_destroy.
+ *  - Work is enqueued on the given stream (a cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and is asynchronous unless stated.
+ *  - Outputs are overwritten, never accumulated into.
+ *  - Return value: LYA_OK (0) or a negative LYA_ERR_* code; lya_last_error()
+ *    gives a message.  Checks that need the data (sorted distances, finite
+ *    values, non-negative weights, consistent offsets) run on the device and
+ *    raise a flag that the next synchronising call (lya_pairs_build,
+ *    lya_sync_status) reports; kernels stay in bounds whatever the data.
+ *  - One handle serves one device and one stream at a time (not thread-safe).
+ */
+#ifndef LYA_H
+#define LYA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LYA_OK = 0,
+  LYA_ERR_INVALID_ARG = -1,   /* bad pointer, size or bin grid */
+  LYA_ERR_UNSORTED = -2,      /* distances not strictly increasing in a forest */
+  LYA_ERR_NONFINITE = -3,     /* NaN/Inf input, or a negative weight */
+  LYA_ERR_NO_MEMORY = -4,     /* device allocation failed */
+  LYA_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+  LYA_ERR_TIMEOUT = -6,       /* reserved: a bounded device wait gave up */
+  LYA_ERR_DEVICE_CHECK = -7,  /* inconsistent offsets seen on the device */
+  LYA_ERR_TOO_LARGE = -8      /* size beyond a documented limit */
+};
+
+typedef struct lya_handle lya_handle;
+
+/* A forest catalogue as flat pixel arrays.  Forest f owns pixels
+ * offsets[f] .. offsets[f+1]-1 (offsets[0] = 0, offsets[n_forests] = n_pix).
+ * Within a forest dist must be strictly increasing (pixels sorted by
+ * wavelength), the source data layout of Section 3.1 with NaN pixels removed. */
+typedef struct {
+  int64_t n_forests;
+  int64_t n_pix;
+  const int64_t* offsets; /* [n_forests+1] */
+  const double* ra;       /* [n_forests] right ascension, radians */
+  const double* dec;      /* [n_forests] declination, radians */
+  const double* dist;     /* [n_pix] comoving distance, Mpc/h */
+  const double* loglam;   /* [n_pix] Lambda = log(lambda), any base */
+  const float* delta;     /* [n_pix] flux-transmission fluctuation, Eq. (2.3) */
+  const float* weight;    /* [n_pix] weight w >= 0 (w = 0 pixels allowed) */
+} lya_catalog;
+
+/* Bin grid of Section 2.1: n_par x n_perp rectangles, D = r_max / n.
+ * Limits: 1 <= n_par <= 512, 1 <= n_perp <= 4096, n_par * n_perp <= 65536. */
+typedef struct {
+  int32_t n_par;
+  int32_t n_perp;
+  double r_par_max;
+  double r_perp_max;
+} lya_bins;
+
+typedef enum {
+  LYA_PREC_FP64 = 0,  /* separations, binning, products and sums in FP64 */
+  LYA_PREC_MIXED = 1  /* FP32 separations/binning/products, FP64 bin sums */
+} lya_precision;
+
+typedef enum {
+  LYA_ETA_IDENTITY = 0,   /* eta = I: D reduces to the identity (a check) */
+  LYA_ETA_MEAN_SLOPE = 1  /* eta of Eq. (2.7): weighted mean and log-lambda slope removed */
+} lya_eta;
+
+/* Create a handle on the current CUDA device.  No device memory is taken
+ * until the first call that needs it.  *out = NULL on failure. */
+int lya_create(lya_handle** out);
+
+/* Release the handle and all its scratch memory.  Synchronises the device. */
+int lya_destroy(lya_handle* h);
+
+/* Copy the last error message (NUL-terminated, truncated to n bytes). */
+int lya_last_error(const lya_handle* h, char* buf, size_t n);
+
+/* Human-readable name of a status code (static string). */
+const char* lya_status_string(int status);
+
+/* Wait for all work on `stream` and report the device-side input checks
+ * raised since the last synchronising call (then clear them). */
+int lya_sync_status(lya_handle* h, void* stream);
+
+/* Forest-pair neighbour list (Section 2.1: only forests within a
+ * neighbourhood set by the maximum separation, found with HEALPix cells,
+ * Section 3.1).  Keeps every unordered pair (a < b) of non-empty forests with
+ * (d_min,a + d_min,b) sin(theta/2) < r_perp_max -- a test that drops only
+ * pairs with no in-grid pixel pair.  The list is cached in the handle for the
+ * (catalogue pointers, sizes, bins) triple and reused by later calls; this
+ * call rebuilds it.  Synchronises `stream`; returns input-check failures.
+ * *n_pairs (host, optional) receives the pair count. */
+int lya_pairs_build(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
+                    int64_t* n_pairs, void* stream);
+
+/* Copy the cached pair list (sorted by (a, b)) into caller device arrays of
+ * capacity `cap`; *n_pairs (host) receives the count.  Synchronises.
+ * Fails with LYA_ERR_INVALID_ARG if no list is cached or cap is too small. */
+int lya_pairs_get(lya_handle* h, int32_t* pair_a, int32_t* pair_b, int64_t cap,
+                  int64_t* n_pairs, void* stream);
+
+/* Continuum projection of Eq. (2.7) applied to delta, forest by forest:
+ * delta' = delta - sum(w delta)/W - x sum(w x delta)/S with x = Lambda - Lbar,
+ * Lbar = sum(w Lambda)/W, W = sum w, S = sum w x^2 (sums in FP64).  S = 0
+ * drops the slope term; W = 0 leaves the forest unchanged.
+ * delta_out: [n_pix] device, may alias cat->delta. */
+int lya_project(lya_handle* h, const lya_catalog* cat, float* delta_out, void* stream);
+
+/* Two-point estimator, Eq. (2.4), over the cached (or freshly built) pair
+ * list.  num[A] = sum (w d)_i (w d)_j, wsum[A] = sum w_i w_j, xi = num/wsum
+ * (0 where wsum = 0), each [n_par*n_perp] float64, A = p*n_perp + t.
+ * Any of num/wsum/xi may be NULL except that xi needs num and wsum.
+ * Builds the pair list (synchronising) if none is cached for these inputs. */
+int lya_xi(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_precision prec,
+           double* num, double* wsum, double* xi, void* stream);
+
+/* Same sums over an explicit forest-pair list (device int32 arrays of n_pairs
+ * pairs; any order; each pair counted once).  Used to evaluate xi on a
+ * sample of the pairs of a large catalogue. */
+int lya_xi_pairs(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_precision prec,
+                 const int32_t* pair_a, const int32_t* pair_b, int64_t n_pairs,
+                 double* num, double* wsum, double* xi, void* stream);
+
+/* Distortion matrix, Eq. (2.6):
+ *   D_AB = W_A^-1 sum_{(i,j) in A} w_i w_j sum_{(k,l) in B} eta_ik eta_jl
+ * over a seeded subsample of the forest pairs (Section 2.2 "a small subset"):
+ * pair (a<b) is kept iff p_subsample >= 1 or
+ * SplitMix64(seed XOR (a*2^32 + b)) < floor(p_subsample * 2^64), SplitMix64
+ * being the first output of the Steele-Lea-Flood generator for that state.
+ * W_A (wsum_dm, [nb] float64, optional) sums w_i w_j over the kept pairs.
+ * dmat: [nb*nb] float64, row A, column B.  Computed from the expansion of
+ * eta = I - rank 2 into per-bin sums (no O(N^4) contraction); FP32 products
+ * with FP64 accumulation.  Limits: nb <= 65536 (dmat is nb^2 doubles). */
+int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_eta eta,
+             double p_subsample, uint64_t seed, double* dmat, double* wsum_dm, void* stream);
+
+/* Gradient of L = sum_A grad_xi[A] xi_A (chain rule of Eq. 2.4):
+ *   dL/d delta_i = w_i sum_j gamma_A (w d)_j,
+ *   dL/d w_i     = delta_i sum_j gamma_A (w d)_j - sum_j gamma_A xi_A w_j,
+ * gamma_A = grad_xi[A] / wsum[A] (0 where wsum = 0), j over in-grid partners.
+ * xi and wsum are the forward outputs for the same inputs (MIXED binning).
+ * grad_delta, grad_weight: [n_pix] float32 device, overwritten. */
+int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
+                    const double* grad_xi, const double* xi, const double* wsum,
+                    float* grad_delta, float* grad_weight, void* stream);
+
+/* xi for n_mocks independent catalogues in one persistent launch.  mocks is a
+ * host array of n_mocks catalogue descriptors (device data each); outputs are
+ * [n_mocks * nb] float64, mock m at offset m*nb.  Pair lists are built per
+ * mock (synchronising) and cached until the inputs change. */
+int lya_xi_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, const lya_bins* bins,
+                   lya_precision prec, double* num, double* wsum, double* xi, void* stream);
+
+/* Tuning: pick launch parameters of the pair kernel by timing candidates on
+ * the cached pair list of `cat` (synchronising); the choice is kept in the
+ * handle for later lya_xi calls with the same bin grid.  *choice (optional,
+ * host) receives an index into the candidate table. */
+int lya_autotune(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int32_t* choice,
+                 void* stream);
+
+/* Diagnostics of the last lya_xi launch (host outputs, synchronising):
+ * the number of forest pairs processed and the launch shape used. */
+int lya_last_launch(lya_handle* h, int64_t* n_pairs, int32_t* grid, int32_t* block,
+                    int32_t* smem_bytes);
+
+/* Work counts of the estimator over the cached pair list, for throughput
+ * reporting (synchronising): over the forest pairs kept by the subsample rule
+ * of lya_dmat (p_subsample >= 1 keeps all), *n_pairs receives the number of
+ * forest pairs, *pixel_pairs the number of in-grid pixel pairs (the terms of
+ * Eq. 2.4, MIXED binning) and *pixel_pairs_sq the sum over forest pairs of
+ * (in-grid pixel pairs)^2 -- the number of terms of the quadruple sum of
+ * Eq. (2.6).  Outputs are host pointers; any may be NULL. */
+int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample,
+                   uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
+                   void* stream);
+
+/* Device time (ms, CUDA events on the launching stream) of the last run of a
+ * stage: 0 = pair kernel of lya_xi / lya_xi_pairs / lya_xi_batched,
+ * 1 = distortion-matrix kernels of lya_dmat, 2 = adjoint kernel of
+ * lya_xi_backward, 3 = pair-list build.  Synchronises.  LYA_ERR_INVALID_ARG
+ * if the stage has not run on this handle. */
+int lya_stage_ms(lya_handle* h, int32_t stage, float* ms);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * since it was loaded (all handles).  Host-only; never fails. */
+int64_t lya_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LYA_H */

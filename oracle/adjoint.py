@@ -19,18 +19,33 @@ from .xi import pixel_pair_bins, xi_sums
 from . import pairs as _pairs
 
 
-def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None):
-    """(dL/d delta, dL/d w, forward sums) for L = sum_A grad_xi[A] xi_A."""
+def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None, absolute: bool = False,
+            eps_edge: float = 0.0, fwd=None):
+    """(dL/d delta, dL/d w, forward sums) for L = sum_A grad_xi[A] xi_A.
+
+    With ``absolute`` the forward dict also holds the same sums taken over the
+    absolute values of the terms (the scale of rounding effects).  With
+    ``eps_edge`` > 0 it holds, per pixel, the largest change of each gradient
+    that moving the pixel pairs whose scaled separations lie within eps_edge
+    of a bin edge into a neighbouring candidate bin can cause (the same
+    candidate bins as ``oracle.xi``).  ``fwd`` may pass precomputed forward
+    sums (num, wsum, xi) to use for gamma and rho."""
     if pair_list is None:
         pair_list = _pairs.forest_pairs(cat, bins)
     d = np.asarray(cat.delta if delta is None else delta, dtype=np.float64)
-    fwd = xi_sums(cat, bins, pair_list, delta=d)
+    if fwd is None:
+        fwd = xi_sums(cat, bins, pair_list, delta=d)
+    fwd = dict(fwd)
     W = fwd["wsum"]
     g = np.asarray(grad_xi, dtype=np.float64)
     gamma = np.divide(g, W, out=np.zeros_like(W), where=W != 0)
     rho = gamma * fwd["xi"]
     gd = np.zeros(cat.n_pix)
     gw = np.zeros(cat.n_pix)
+    gda = np.zeros(cat.n_pix)
+    gwa = np.zeros(cat.n_pix)
+    ega = np.zeros(cat.n_pix)
+    ewa = np.zeros(cat.n_pix)
     w_all = cat.weight.astype(np.float64)
     nvec = unit_vectors(cat.ra, cat.dec)
     for a, b in zip(*pair_list):
@@ -38,7 +53,7 @@ def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None):
         if sa.stop == sa.start or sb.stop == sb.start:
             continue
         c, s = half_angle(nvec[a], nvec[b])
-        A, ok, _, _ = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
+        A, ok, x, y = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
         G = np.where(ok, gamma[np.maximum(A, 0)], 0.0)
         R = np.where(ok, rho[np.maximum(A, 0)], 0.0)
         wa, wb = w_all[sa], w_all[sb]
@@ -52,6 +67,39 @@ def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None):
         gd[sb] += wb * gb
         gw[sa] += da * ga - ra
         gw[sb] += db * gb - rb
+        if eps_edge > 0.0:
+            # largest |gamma'-gamma|, |rho'-rho| over the candidate bins of each ambiguous pair
+            p_lo = np.floor(np.maximum(x - eps_edge, 0.0))
+            p_hi = np.floor(x + eps_edge)
+            t_lo = np.floor(np.maximum(y - eps_edge, 0.0))
+            t_hi = np.floor(y + eps_edge)
+            amb = (p_lo != p_hi) | (t_lo != t_hi)
+            dG = np.zeros_like(G)
+            dR = np.zeros_like(R)
+            if np.any(amb):
+                for pp, tt in ((p_lo, t_lo), (p_hi, t_lo), (p_lo, t_hi), (p_hi, t_hi)):
+                    inside = (pp < bins.n_par) & (tt < bins.n_perp)
+                    idx = np.where(inside, pp * bins.n_perp + tt, 0).astype(np.int64)
+                    gc = np.where(inside, gamma[idx], 0.0)
+                    rc = np.where(inside, rho[idx], 0.0)
+                    dG = np.where(amb, np.maximum(dG, np.abs(gc - G)), dG)
+                    dR = np.where(amb, np.maximum(dR, np.abs(rc - R)), dR)
+            ega[sa] += np.abs(wa) * (dG @ np.abs(wdb))
+            ega[sb] += np.abs(wb) * (dG.T @ np.abs(wda))
+            ewa[sa] += np.abs(da) * (dG @ np.abs(wdb)) + dR @ np.abs(wb)
+            ewa[sb] += np.abs(db) * (dG.T @ np.abs(wda)) + dR.T @ np.abs(wa)
+        if absolute:
+            Ga, Ra = np.abs(G), np.abs(R)
+            gda[sa] += np.abs(wa) * (Ga @ np.abs(wdb))
+            gda[sb] += np.abs(wb) * (Ga.T @ np.abs(wda))
+            gwa[sa] += np.abs(da) * (Ga @ np.abs(wdb)) + Ra @ np.abs(wb)
+            gwa[sb] += np.abs(db) * (Ga.T @ np.abs(wda)) + Ra.T @ np.abs(wa)
+    if absolute:
+        fwd["grad_delta_abs"] = gda
+        fwd["grad_weight_abs"] = gwa
+    if eps_edge > 0.0:
+        fwd["grad_delta_edge"] = ega
+        fwd["grad_weight_edge"] = ewa
     return gd, gw, fwd
 
 

@@ -1,0 +1,277 @@
+"""Python face of liblya.so: device catalogues, a handle, one function per C
+entry point (same names), and a torch.autograd.Function for xi.
+
+PyTorch provides device memory and the current stream; every computation
+runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import LyaBins, LyaCatalog, check
+
+PREC = {"mixed": _lib.LYA_PREC_MIXED, "fp64": _lib.LYA_PREC_FP64}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class DeviceCatalog:
+    """A forest catalogue resident on the GPU (layout of ``lya_catalog``)."""
+
+    def __init__(self, offsets, ra, dec, dist, loglam, delta, weight):
+        self.offsets = offsets.contiguous()
+        self.ra = ra.contiguous()
+        self.dec = dec.contiguous()
+        self.dist = dist.contiguous()
+        self.loglam = loglam.contiguous()
+        self.delta = delta.contiguous()
+        self.weight = weight.contiguous()
+        assert self.offsets.dtype == torch.int64
+        for t in (self.ra, self.dec, self.dist, self.loglam):
+            assert t.dtype == torch.float64
+        for t in (self.delta, self.weight):
+            assert t.dtype == torch.float32
+
+    @property
+    def n_forests(self) -> int:
+        return int(self.ra.shape[0])
+
+    @property
+    def n_pix(self) -> int:
+        return int(self.dist.shape[0])
+
+    @classmethod
+    def from_host(cls, cat, device="cuda", pin: bool = False) -> "DeviceCatalog":
+        def t(a, dt):
+            x = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
+            if pin:
+                x = x.pin_memory()
+            return x.to(device, non_blocking=pin)
+        return cls(t(cat.offsets, torch.int64), t(cat.ra, torch.float64), t(cat.dec, torch.float64),
+                   t(cat.dist, torch.float64), t(cat.loglam, torch.float64), t(cat.delta, torch.float32),
+                   t(cat.weight, torch.float32))
+
+    def with_(self, delta=None, weight=None) -> "DeviceCatalog":
+        return DeviceCatalog(self.offsets, self.ra, self.dec, self.dist, self.loglam,
+                             self.delta if delta is None else delta,
+                             self.weight if weight is None else weight)
+
+    def c(self) -> LyaCatalog:
+        return LyaCatalog(self.n_forests, self.n_pix, self.offsets.data_ptr(), self.ra.data_ptr(),
+                          self.dec.data_ptr(), self.dist.data_ptr(), self.loglam.data_ptr(),
+                          self.delta.data_ptr(), self.weight.data_ptr())
+
+
+def c_bins(bins) -> LyaBins:
+    return LyaBins(int(bins.n_par), int(bins.n_perp), float(bins.r_par_max), float(bins.r_perp_max))
+
+
+class Handle:
+    """Owns an ``lya_handle`` (scratch memory, cached pair list)."""
+
+    def __init__(self):
+        lib = _lib.load()
+        h = ctypes.c_void_p()
+        rc = lib.lya_create(ctypes.byref(h))
+        if rc != 0:
+            raise _lib.LyaError(rc, "lya_create failed (no CUDA device?)")
+        self._h = h
+
+    @property
+    def h(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.load().lya_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# one function per C entry point (same names); tensors are CUDA tensors
+# ---------------------------------------------------------------------------
+def lya_sync_status(handle: Handle, stream=None):
+    check(handle.h, _lib.load().lya_sync_status(handle.h, _stream(stream)))
+
+
+def lya_pairs_build(handle: Handle, cat: DeviceCatalog, bins, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_pairs_build(handle.h, ctypes.byref(c), ctypes.byref(b),
+                                                ctypes.byref(n), _stream(stream)))
+    return int(n.value)
+
+
+def lya_pairs_get(handle: Handle, n_pairs: int, stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    a = torch.empty(max(n_pairs, 1), dtype=torch.int32, device="cuda")
+    b = torch.empty(max(n_pairs, 1), dtype=torch.int32, device="cuda")
+    n = ctypes.c_int64(0)
+    check(handle.h, _lib.load().lya_pairs_get(handle.h, _ptr(a), _ptr(b), n_pairs, ctypes.byref(n),
+                                              _stream(stream)))
+    return a[: n.value], b[: n.value]
+
+
+def lya_project(handle: Handle, cat: DeviceCatalog, out: Optional[torch.Tensor] = None, stream=None):
+    out = torch.empty_like(cat.delta) if out is None else out
+    c = cat.c()
+    check(handle.h, _lib.load().lya_project(handle.h, ctypes.byref(c), _ptr(out), _stream(stream)))
+    return out
+
+
+def lya_xi(handle: Handle, cat: DeviceCatalog, bins, precision: str = "mixed", num=None, wsum=None,
+           xi=None, stream=None):
+    nb = bins.n_par * bins.n_perp
+    num = torch.empty(nb, dtype=torch.float64, device="cuda") if num is None else num
+    wsum = torch.empty(nb, dtype=torch.float64, device="cuda") if wsum is None else wsum
+    xi = torch.empty(nb, dtype=torch.float64, device="cuda") if xi is None else xi
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi(handle.h, ctypes.byref(c), ctypes.byref(b), PREC[precision],
+                                       _ptr(num), _ptr(wsum), _ptr(xi), _stream(stream)))
+    return num, wsum, xi
+
+
+def lya_xi_pairs(handle: Handle, cat: DeviceCatalog, bins, pair_a: torch.Tensor, pair_b: torch.Tensor,
+                 precision: str = "mixed", stream=None):
+    nb = bins.n_par * bins.n_perp
+    num = torch.empty(nb, dtype=torch.float64, device="cuda")
+    wsum = torch.empty(nb, dtype=torch.float64, device="cuda")
+    xi = torch.empty(nb, dtype=torch.float64, device="cuda")
+    pa = pair_a.to(torch.int32).contiguous()
+    pb = pair_b.to(torch.int32).contiguous()
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_pairs(handle.h, ctypes.byref(c), ctypes.byref(b), PREC[precision],
+                                             _ptr(pa), _ptr(pb), int(pa.numel()), _ptr(num), _ptr(wsum),
+                                             _ptr(xi), _stream(stream)))
+    return num, wsum, xi
+
+
+def lya_dmat(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed: int,
+             eta: str = "mean_slope", stream=None):
+    nb = bins.n_par * bins.n_perp
+    D = torch.empty((nb, nb), dtype=torch.float64, device="cuda")
+    W = torch.empty(nb, dtype=torch.float64, device="cuda")
+    e = _lib.LYA_ETA_MEAN_SLOPE if eta == "mean_slope" else _lib.LYA_ETA_IDENTITY
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_dmat(handle.h, ctypes.byref(c), ctypes.byref(b), e, float(p_subsample),
+                                         ctypes.c_uint64(seed), _ptr(D), _ptr(W), _stream(stream)))
+    return D, W
+
+
+def lya_xi_backward(handle: Handle, cat: DeviceCatalog, bins, grad_xi: torch.Tensor, xi: torch.Tensor,
+                    wsum: torch.Tensor, stream=None):
+    gd = torch.empty_like(cat.delta)
+    gw = torch.empty_like(cat.weight)
+    g = grad_xi.to(torch.float64).contiguous()
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_backward(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(g),
+                                                _ptr(xi.contiguous()), _ptr(wsum.contiguous()), _ptr(gd),
+                                                _ptr(gw), _stream(stream)))
+    return gd, gw
+
+
+def lya_xi_batched(handle: Handle, mocks: Sequence[DeviceCatalog], bins, precision: str = "mixed",
+                   stream=None):
+    nb = bins.n_par * bins.n_perp
+    m = len(mocks)
+    num = torch.empty(m * nb, dtype=torch.float64, device="cuda")
+    wsum = torch.empty(m * nb, dtype=torch.float64, device="cuda")
+    xi = torch.empty(m * nb, dtype=torch.float64, device="cuda")
+    arr = (LyaCatalog * m)(*[c.c() for c in mocks])
+    b = c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_batched(handle.h, arr, m, ctypes.byref(b), PREC[precision], _ptr(num),
+                                               _ptr(wsum), _ptr(xi), _stream(stream)))
+    return num.view(m, nb), wsum.view(m, nb), xi.view(m, nb)
+
+
+def lya_autotune(handle: Handle, cat: DeviceCatalog, bins, stream=None) -> int:
+    ch = ctypes.c_int32(-1)
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_autotune(handle.h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(ch),
+                                             _stream(stream)))
+    return int(ch.value)
+
+
+def lya_last_launch(handle: Handle):
+    n, g, bl, sm = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(handle.h, _lib.load().lya_last_launch(handle.h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(bl),
+                                                ctypes.byref(sm)))
+    return {"pairs": n.value, "grid": g.value, "block": bl.value, "smem": sm.value}
+
+
+def lya_pair_stats(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float = 1.0, seed: int = 0,
+                   stream=None):
+    n, pix, sq = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_pair_stats(handle.h, ctypes.byref(c), ctypes.byref(b), float(p_subsample),
+                                               ctypes.c_uint64(seed), ctypes.byref(n), ctypes.byref(pix),
+                                               ctypes.byref(sq), _stream(stream)))
+    return {"forest_pairs": n.value, "pixel_pairs": pix.value, "pixel_pairs_sq": sq.value}
+
+
+STAGES = {"xi": 0, "dmat": 1, "adjoint": 2, "pairs": 3}
+
+
+def lya_stage_ms(handle: Handle, stage: str) -> float:
+    ms = ctypes.c_float()
+    check(handle.h, _lib.load().lya_stage_ms(handle.h, STAGES[stage], ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def lya_kernel_launches() -> int:
+    return int(_lib.load().lya_kernel_launches())
+
+
+# ---------------------------------------------------------------------------
+# autograd
+# ---------------------------------------------------------------------------
+class XiFunction(torch.autograd.Function):
+    """(xi, W) = estimator of Eq. (2.4) as a differentiable function of (delta, w)."""
+
+    @staticmethod
+    def forward(ctx, delta, weight, handle, cat, bins):
+        c = cat.with_(delta=delta.detach().contiguous(), weight=weight.detach().contiguous())
+        num, wsum, xi = lya_xi(handle, c, bins, "mixed")
+        ctx.handle, ctx.cat, ctx.bins = handle, c, bins
+        ctx.save_for_backward(xi, wsum)
+        ctx.mark_non_differentiable(wsum)
+        return xi, wsum
+
+    @staticmethod
+    def backward(ctx, grad_xi, grad_wsum):
+        xi, wsum = ctx.saved_tensors
+        if grad_xi is None:
+            return None, None, None, None, None
+        gd, gw = lya_xi_backward(ctx.handle, ctx.cat, ctx.bins, grad_xi, xi, wsum)
+        return gd, gw, None, None, None
+
+
+def xi(cat: DeviceCatalog, bins, handle: Optional[Handle] = None, delta=None, weight=None):
+    """Differentiable (xi, W) for the catalogue (delta / weight may be leaf tensors)."""
+    handle = handle or Handle()
+    d = cat.delta if delta is None else delta
+    w = cat.weight if weight is None else weight
+    return XiFunction.apply(d, w, handle, cat, bins)

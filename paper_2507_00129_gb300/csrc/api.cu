@@ -1,0 +1,775 @@
+// C ABI of liblya.so (declared in include/lya.h): handle, scratch memory,
+// argument checks and the orchestration of the kernels of prep.cu, pairs.cu,
+// xi.cu, dmat.cu and adjoint.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lya_internal.cuh"
+
+#include <atomic>
+
+namespace lya {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t grow(void** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return cudaSuccess;
+  if (*p) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  size_t n = need + need / 4 + 256;
+  cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  *cap = n;
+  return cudaSuccess;
+}
+
+namespace {
+
+__global__ void min_dmin_kernel(Forests F, unsigned long long* out) {
+  // distances are positive: their IEEE bit patterns order like the values
+  unsigned long long m = ~0ull;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F.n;
+       f += (int64_t)gridDim.x * blockDim.x)
+    if (F.len[f] > 0 && F.dmin[f] > 0.0)
+      m = min(m, static_cast<unsigned long long>(__double_as_longlong(F.dmin[f])));
+  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
+__global__ void check_pairs_kernel(int2* p, int64_t n, int64_t nf, unsigned* err) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 q = p[k];
+    if (q.x < 0 || q.y < 0 || q.x >= nf || q.y >= nf || q.x == q.y) {
+      p[k] = make_int2(-1, -1);
+      atomicOr(err, FLAG_OFFSETS);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace lya
+
+using namespace lya;
+
+struct CatKey {
+  std::vector<const void*> ptrs;
+  std::vector<int64_t> sizes;
+  int32_t n_par = 0, n_perp = 0;
+  double rpar = 0, rperp = 0;
+  bool operator==(const CatKey& o) const {
+    return ptrs == o.ptrs && sizes == o.sizes && n_par == o.n_par && n_perp == o.n_perp &&
+           rpar == o.rpar && rperp == o.rperp;
+  }
+};
+
+struct lya_handle {
+  int device = 0;
+  DevInfo dev{};
+  std::string err;
+  unsigned* d_err = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int32_t* d_i32 = nullptr;
+  unsigned long long* d_u64 = nullptr;
+  // workspace catalogue (union of all mocks)
+  void* fbuf = nullptr;
+  size_t fbuf_cap = 0;
+  Forests F{};
+  int64_t F_capacity = 0;
+  void* pixbuf = nullptr;
+  size_t pix_cap = 0;
+  // pair list cache
+  void* pairbuf = nullptr;     // int2 pairs (grown by build_pairs)
+  int64_t pair_cap = 0;
+  int64_t n_pairs = 0;
+  void* csbuf = nullptr;
+  size_t cs_cap = 0;
+  bool pairs_valid = false;
+  CatKey key;
+  unsigned long long* d_fp = nullptr;   // geometry fingerprint of the last prepare()
+  unsigned long long fp_cached = 0;     // fingerprint the cached pair list was built for
+  int max_len = 0;
+  int n_mocks = 1;
+  // scratch
+  void* scratch = nullptr;
+  size_t scratch_cap = 0;
+  void* scratch2 = nullptr;
+  size_t scratch2_cap = 0;
+  void* outbuf = nullptr;      // num/wsum when the caller passes NULL
+  size_t out_cap = 0;
+  void* gbuf = nullptr;        // D accumulator
+  size_t g_cap = 0;
+  // tuning and diagnostics
+  int tuned_warps = 8;
+  int tuned_grab = 4;
+  int tuned_for_npar = -1;
+  XiLaunch last{};
+  int64_t last_pairs = 0;
+  // stage timing events: [stage][begin, end]
+  cudaEvent_t ev[4][2] = {};
+  bool ev_used[4] = {false, false, false, false};
+};
+
+namespace {
+
+void stage_begin(lya_handle* h, int k, cudaStream_t s) { cudaEventRecord(h->ev[k][0], s); }
+void stage_end(lya_handle* h, int k, cudaStream_t s) {
+  cudaEventRecord(h->ev[k][1], s);
+  h->ev_used[k] = true;
+}
+
+int fail(lya_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(lya_handle* h, cudaError_t e, const char* where) {
+  return fail(h, LYA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+int check_bins(lya_handle* h, const lya_bins* b) {
+  if (!b) return fail(h, LYA_ERR_INVALID_ARG, "bins is NULL");
+  if (b->n_par < 1 || b->n_par > 512 || b->n_perp < 1 || b->n_perp > 4096 ||
+      static_cast<int64_t>(b->n_par) * b->n_perp > 65536)
+    return fail(h, LYA_ERR_TOO_LARGE, "bin grid outside 1..512 x 1..4096 (<= 65536 bins)");
+  if (!(b->r_par_max > 0) || !(b->r_perp_max > 0) || !std::isfinite(b->r_par_max) ||
+      !std::isfinite(b->r_perp_max))
+    return fail(h, LYA_ERR_INVALID_ARG, "r_par_max and r_perp_max must be finite and > 0");
+  return LYA_OK;
+}
+
+int check_cat(lya_handle* h, const lya_catalog* c) {
+  if (!c) return fail(h, LYA_ERR_INVALID_ARG, "catalogue is NULL");
+  if (c->n_forests < 0 || c->n_pix < 0) return fail(h, LYA_ERR_INVALID_ARG, "negative size");
+  if (c->n_forests >= (1LL << 31) - 1) return fail(h, LYA_ERR_TOO_LARGE, "more than 2^31-2 forests");
+  if (!c->offsets) return fail(h, LYA_ERR_INVALID_ARG, "offsets is NULL");
+  if (c->n_forests > 0 && (!c->ra || !c->dec))
+    return fail(h, LYA_ERR_INVALID_ARG, "ra/dec is NULL");
+  if (c->n_pix > 0 && (!c->dist || !c->loglam || !c->delta || !c->weight))
+    return fail(h, LYA_ERR_INVALID_ARG, "pixel array is NULL");
+  return LYA_OK;
+}
+
+int flags_to_status(lya_handle* h, unsigned f) {
+  if (f == 0) return LYA_OK;
+  std::string m = "input check failed:";
+  int code = LYA_ERR_DEVICE_CHECK;
+  if (f & FLAG_OFFSETS) { m += " inconsistent offsets or pair indices;"; code = LYA_ERR_DEVICE_CHECK; }
+  if (f & FLAG_TOO_LONG) { m += " forest longer than 2^20 pixels;"; code = LYA_ERR_TOO_LARGE; }
+  if (f & FLAG_NEGATIVE_W) { m += " negative weight;"; code = LYA_ERR_NONFINITE; }
+  if (f & FLAG_NONFINITE) { m += " non-finite or non-positive value;"; code = LYA_ERR_NONFINITE; }
+  if (f & FLAG_UNSORTED) { m += " distances not strictly increasing within a forest;"; code = LYA_ERR_UNSORTED; }
+  return fail(h, code, m);
+}
+
+int read_flags(lya_handle* h, cudaStream_t s, unsigned* out) {
+  CK(cudaMemcpyAsync(out, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "read flags");
+  CK(cudaStreamSynchronize(s), "sync");
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), s), "clear flags");
+  return LYA_OK;
+}
+
+// Forest and pixel workspace for n forests / p pixels.  Reallocates (losing
+// the cached pair list) only when capacity is short.
+int ensure_workspace(lya_handle* h, int64_t nf, int64_t np) {
+  if (nf > h->F_capacity || !h->fbuf) {
+    const int64_t cap = std::max<int64_t>(nf, 1) + std::max<int64_t>(nf, 1) / 4;
+    const size_t bytes = static_cast<size_t>(cap) * (8 * 9 + 4 * 3) + 16 * 64;
+    if (h->fbuf) { cudaDeviceSynchronize(); cudaFree(h->fbuf); h->fbuf = nullptr; }
+    cudaError_t e = cudaMalloc(&h->fbuf, bytes);
+    if (e != cudaSuccess) { h->F_capacity = 0; return fail(h, LYA_ERR_NO_MEMORY, "forest workspace"); }
+    h->fbuf_cap = bytes;
+    char* p = static_cast<char*>(h->fbuf);
+    auto take = [&](size_t b) { char* q = p; p += (b + 255) & ~size_t(255); return q; };
+    h->F.off = reinterpret_cast<int64_t*>(take(cap * 8));
+    h->F.ux = reinterpret_cast<double*>(take(cap * 8));
+    h->F.uy = reinterpret_cast<double*>(take(cap * 8));
+    h->F.uz = reinterpret_cast<double*>(take(cap * 8));
+    h->F.dmin = reinterpret_cast<double*>(take(cap * 8));
+    h->F.dmax = reinterpret_cast<double*>(take(cap * 8));
+    h->F.wsum = reinterpret_cast<double*>(take(cap * 8));
+    h->F.lbar = reinterpret_cast<double*>(take(cap * 8));
+    h->F.ssum = reinterpret_cast<double*>(take(cap * 8));
+    h->F.len = reinterpret_cast<int32_t*>(take(cap * 4));
+    h->F.dref = reinterpret_cast<float*>(take(cap * 4));
+    h->F.mock = reinterpret_cast<int32_t*>(take(cap * 4));
+    h->F_capacity = cap;
+    h->pairs_valid = false;
+  }
+  h->F.n = nf;
+  cudaError_t e = grow(&h->pixbuf, &h->pix_cap, static_cast<size_t>(std::max<int64_t>(np, 1)) * 16);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "pixel workspace");
+  return LYA_OK;
+}
+
+CatKey make_key(const lya_catalog* cats, int n, const lya_bins* b) {
+  CatKey k;
+  for (int m = 0; m < n; ++m) {
+    k.ptrs.push_back(cats[m].ra);
+    k.ptrs.push_back(cats[m].dec);
+    k.ptrs.push_back(cats[m].dist);
+    k.ptrs.push_back(cats[m].offsets);
+    k.sizes.push_back(cats[m].n_forests);
+    k.sizes.push_back(cats[m].n_pix);
+  }
+  k.n_par = b->n_par;
+  k.n_perp = b->n_perp;
+  k.rpar = b->r_par_max;
+  k.rperp = b->r_perp_max;
+  return k;
+}
+
+// Prepare all catalogues (input checks, moments, packed pixels).  Async.
+int prepare(lya_handle* h, const lya_catalog* cats, int n, cudaStream_t s) {
+  int64_t nf = 0, np = 0;
+  for (int m = 0; m < n; ++m) {
+    int st = check_cat(h, &cats[m]);
+    if (st) return st;
+    nf += cats[m].n_forests;
+    np += cats[m].n_pix;
+  }
+  if (nf >= (1LL << 31) - 1) return fail(h, LYA_ERR_TOO_LARGE, "more than 2^31-2 forests");
+  int st = ensure_workspace(h, nf, np);
+  if (st) return st;
+  int64_t fb = 0, pb = 0;
+  CK(cudaMemsetAsync(h->d_fp, 0, sizeof(unsigned long long), s), "clear fingerprint");
+  for (int m = 0; m < n; ++m) {
+    CK(launch_prep(cats[m], fb, pb, m, h->F, static_cast<Pix*>(h->pixbuf), h->d_err, h->d_fp, s), "prep");
+    fb += cats[m].n_forests;
+    pb += cats[m].n_pix;
+  }
+  return LYA_OK;
+}
+
+int build_all_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bins* b, cudaStream_t s) {
+  h->pairs_valid = false;
+  stage_begin(h, 3, s);
+  // catalogue-wide angle bound from the smallest distance
+  CK(cudaMemsetAsync(h->d_u64, 0xff, 8, s), "memset");
+  if (h->F.n > 0) {
+    int64_t blocks = std::min<int64_t>((h->F.n + 255) / 256, 4096);
+    LYA_COUNT(1), min_dmin_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(h->F, h->d_u64);
+    CK(cudaGetLastError(), "min_dmin");
+  }
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, h->d_u64, 8, cudaMemcpyDeviceToHost, s), "read dmin");
+  CK(launch_max_len(h->F, h->d_i32, s), "max_len");
+  int32_t ml = 0;
+  CK(cudaMemcpyAsync(&ml, h->d_i32, 4, cudaMemcpyDeviceToHost, s), "read max_len");
+  unsigned flags = 0;
+  int st = read_flags(h, s, &flags);
+  if (st) return st;
+  st = flags_to_status(h, flags);
+  if (st) return st;
+  h->max_len = ml;
+  double dmin = 1.0;
+  if (bits != ~0ull) std::memcpy(&dmin, &bits, 8);
+  const double th = 2.0 * std::asin(std::min(1.0, b->r_perp_max / (2.0 * dmin)));
+  const double th_deg = th * 180.0 / M_PI;
+  int nside = 1;
+  while (nside < 256 && 117.0 / th_deg >= 2.0 * nside) nside *= 2;
+  PairBuild pbld{nside, b->r_perp_max, th};
+  int64_t total = 0, fb = 0;
+  int2* pairs = static_cast<int2*>(h->pairbuf);
+  for (int m = 0; m < n; ++m) {
+    int64_t got = 0;
+    CK(build_pairs(h->F, fb, fb + cats[m].n_forests, pbld, &pairs, &h->pair_cap, total, &got,
+                   &h->scratch, &h->scratch_cap, s),
+       "pair list");
+    total += got;
+    fb += cats[m].n_forests;
+  }
+  h->pairbuf = pairs;
+  h->n_pairs = total;
+  cudaError_t e = grow(&h->csbuf, &h->cs_cap, static_cast<size_t>(std::max<int64_t>(total, 1)) * 8);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "pair geometry");
+  CK(launch_pair_geometry(pairs, total, h->F, b->n_par / b->r_par_max, b->n_perp / b->r_perp_max,
+                          static_cast<float2*>(h->csbuf), s),
+     "pair geometry");
+  stage_end(h, 3, s);
+  unsigned long long fp = 0;
+  CK(cudaMemcpyAsync(&fp, h->d_fp, 8, cudaMemcpyDeviceToHost, s), "read fingerprint");
+  CK(cudaStreamSynchronize(s), "sync");
+  h->fp_cached = fp;
+  h->key = make_key(cats, n, b);
+  h->n_mocks = n;
+  h->pairs_valid = true;
+  return LYA_OK;
+}
+
+// Reuse the cached pair list only if the pointers, sizes and bins match AND
+// the geometry fingerprint of this call's prepare() equals the one the list
+// was built for (freed device memory is often handed out again at the same
+// address, so pointers alone do not identify a catalogue).  The fingerprint
+// read synchronises the stream.
+int ensure_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bins* b, cudaStream_t s) {
+  if (h->pairs_valid && h->key == make_key(cats, n, b)) {
+    unsigned long long fp = 0;
+    CK(cudaMemcpyAsync(&fp, h->d_fp, 8, cudaMemcpyDeviceToHost, s), "read fingerprint");
+    CK(cudaStreamSynchronize(s), "sync");
+    if (fp == h->fp_cached) return LYA_OK;
+  }
+  return build_all_pairs(h, cats, n, b, s);
+}
+
+int run_xi(lya_handle* h, const lya_catalog* cats, int ncat, const lya_bins* b, lya_precision prec,
+           const int2* pairs, const float2* cs, int64_t npairs, double* num, double* wsum, double* xi,
+           cudaStream_t s) {
+  const int nb = b->n_par * b->n_perp;
+  const int64_t nout = static_cast<int64_t>(nb) * ncat;
+  double* N = num;
+  double* W = wsum;
+  if (!N || !W) {
+    cudaError_t e = grow(&h->outbuf, &h->out_cap, static_cast<size_t>(nout) * 16);
+    if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "output scratch");
+    if (!N) N = static_cast<double*>(h->outbuf);
+    if (!W) W = static_cast<double*>(h->outbuf) + nout;
+  }
+  CK(cudaMemsetAsync(N, 0, nout * 8, s), "zero num");
+  CK(cudaMemsetAsync(W, 0, nout * 8, s), "zero wsum");
+  XiArgs A;
+  A.pairs = pairs;
+  A.cs = cs;
+  A.n_pairs = npairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = b->n_par;
+  A.n_perp = b->n_perp;
+  A.num = N;
+  A.wsum = W;
+  A.nb = nb;
+  A.counter = h->d_counter;
+  if (prec == LYA_PREC_MIXED) {
+    XiLaunch L;
+    const int warps = (h->tuned_for_npar == b->n_par) ? h->tuned_warps : 8;
+    const int grab = (h->tuned_for_npar == b->n_par) ? h->tuned_grab : 4;
+    CK(plan_xi_mixed(h->dev, b->n_par, h->max_len, warps, grab, &L), "plan xi");
+    stage_begin(h, 0, s);
+    CK(launch_xi_mixed(A, L, s), "xi kernel");
+    stage_end(h, 0, s);
+    h->last = L;
+  } else if (prec == LYA_PREC_FP64) {
+    XiLaunch L{};
+    stage_begin(h, 0, s);
+    CK(launch_xi_fp64(A, cats, ncat, h->dev, h->max_len, b->r_par_max, b->r_perp_max, &L, s),
+       "xi fp64 kernel");
+    stage_end(h, 0, s);
+    h->last = L;
+  } else {
+    return fail(h, LYA_ERR_INVALID_ARG, "unknown precision");
+  }
+  h->last_pairs = npairs;
+  if (xi) CK(launch_finalize(N, W, xi, nout, s), "finalize");
+  return LYA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lya_create(lya_handle** out) {
+  if (!out) return LYA_ERR_INVALID_ARG;
+  *out = nullptr;
+  lya_handle* h = new lya_handle();
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->dev.sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->dev.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->dev.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+  void* small = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&small, 512);
+  if (e == cudaSuccess) e = cudaMemset(small, 0, 512);
+  if (e != cudaSuccess) {
+    if (small) cudaFree(small);
+    delete h;
+    return LYA_ERR_CUDA;
+  }
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreate(&h->ev[k][q]);
+  if (e != cudaSuccess) {
+    cudaFree(small);
+    delete h;
+    return LYA_ERR_CUDA;
+  }
+  char* p = static_cast<char*>(small);
+  h->d_err = reinterpret_cast<unsigned*>(p);
+  h->d_counter = reinterpret_cast<unsigned long long*>(p + 64);
+  h->d_i32 = reinterpret_cast<int32_t*>(p + 128);
+  h->d_u64 = reinterpret_cast<unsigned long long*>(p + 192);
+  h->d_fp = reinterpret_cast<unsigned long long*>(p + 256);
+  *out = h;
+  return LYA_OK;
+}
+
+int lya_destroy(lya_handle* h) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  void* bufs[] = {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
+                  h->d_err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int k = 0; k < 4; ++k)
+    for (int q = 0; q < 2; ++q)
+      if (h->ev[k][q]) cudaEventDestroy(h->ev[k][q]);
+  delete h;
+  return LYA_OK;
+}
+
+int lya_last_error(const lya_handle* h, char* buf, size_t n) {
+  if (!h || !buf || n == 0) return LYA_ERR_INVALID_ARG;
+  std::snprintf(buf, n, "%s", h->err.c_str());
+  return LYA_OK;
+}
+
+const char* lya_status_string(int s) {
+  switch (s) {
+    case LYA_OK: return "LYA_OK";
+    case LYA_ERR_INVALID_ARG: return "LYA_ERR_INVALID_ARG";
+    case LYA_ERR_UNSORTED: return "LYA_ERR_UNSORTED";
+    case LYA_ERR_NONFINITE: return "LYA_ERR_NONFINITE";
+    case LYA_ERR_NO_MEMORY: return "LYA_ERR_NO_MEMORY";
+    case LYA_ERR_CUDA: return "LYA_ERR_CUDA";
+    case LYA_ERR_TIMEOUT: return "LYA_ERR_TIMEOUT";
+    case LYA_ERR_DEVICE_CHECK: return "LYA_ERR_DEVICE_CHECK";
+    case LYA_ERR_TOO_LARGE: return "LYA_ERR_TOO_LARGE";
+    default: return "LYA_ERR_UNKNOWN";
+  }
+}
+
+int lya_sync_status(lya_handle* h, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned flags = 0;
+  int st = read_flags(h, s, &flags);
+  if (st) return st;
+  return flags_to_status(h, flags);
+}
+
+int lya_pairs_build(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int64_t* n_pairs,
+                    void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = build_all_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  if (n_pairs) *n_pairs = h->n_pairs;
+  return LYA_OK;
+}
+
+int lya_pairs_get(lya_handle* h, int32_t* pair_a, int32_t* pair_b, int64_t cap, int64_t* n_pairs,
+                  void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (!h->pairs_valid) return fail(h, LYA_ERR_INVALID_ARG, "no pair list cached");
+  if (n_pairs) *n_pairs = h->n_pairs;
+  if (cap < h->n_pairs) return fail(h, LYA_ERR_INVALID_ARG, "capacity too small");
+  if (h->n_pairs > 0 && (!pair_a || !pair_b)) return fail(h, LYA_ERR_INVALID_ARG, "NULL output");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(launch_unpack_pairs(static_cast<const int2*>(h->pairbuf), h->n_pairs, pair_a, pair_b, s), "unpack");
+  CK(cudaStreamSynchronize(s), "sync");
+  return LYA_OK;
+}
+
+int lya_project(lya_handle* h, const lya_catalog* cat, float* delta_out, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (!delta_out && cat && cat->n_pix > 0) return fail(h, LYA_ERR_INVALID_ARG, "delta_out is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = prepare(h, cat, 1, s);
+  if (st) return st;
+  CK(launch_project(*cat, h->F, 0, delta_out, s), "project");
+  return LYA_OK;
+}
+
+int lya_xi(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_precision prec, double* num,
+           double* wsum, double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!num && !wsum && !xi) return fail(h, LYA_ERR_INVALID_ARG, "no output requested");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  return run_xi(h, cat, 1, bins, prec, static_cast<const int2*>(h->pairbuf),
+                static_cast<const float2*>(h->csbuf), h->n_pairs, num, wsum, xi, s);
+}
+
+int lya_xi_pairs(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_precision prec,
+                 const int32_t* pair_a, const int32_t* pair_b, int64_t n_pairs, double* num, double* wsum,
+                 double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (n_pairs < 0 || (n_pairs > 0 && (!pair_a || !pair_b)))
+    return fail(h, LYA_ERR_INVALID_ARG, "bad pair arrays");
+  if (!num && !wsum && !xi) return fail(h, LYA_ERR_INVALID_ARG, "no output requested");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  // the explicit list is used as given; the cached list (if any) is left alone
+  CK(launch_max_len(h->F, h->d_i32, s), "max_len");
+  int32_t ml = 0;
+  CK(cudaMemcpyAsync(&ml, h->d_i32, 4, cudaMemcpyDeviceToHost, s), "read max_len");
+  CK(cudaStreamSynchronize(s), "sync");
+  const int saved = h->max_len;
+  h->max_len = ml;
+  cudaError_t e = grow(&h->scratch2, &h->scratch2_cap, static_cast<size_t>(std::max<int64_t>(n_pairs, 1)) * 16);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "pair scratch");
+  int2* pp = static_cast<int2*>(h->scratch2);
+  float2* cs = reinterpret_cast<float2*>(pp + std::max<int64_t>(n_pairs, 1));
+  CK(launch_pack_pairs(pair_a, pair_b, n_pairs, pp, s), "pack pairs");
+  if (n_pairs > 0) {
+    int64_t blocks = std::min<int64_t>((n_pairs + 255) / 256, 65535);
+    LYA_COUNT(1), check_pairs_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(pp, n_pairs, cat->n_forests, h->d_err);
+    CK(cudaGetLastError(), "check pairs");
+  }
+  // invalid pairs were replaced by (-1,-1); the geometry and xi kernels skip them
+  CK(launch_pair_geometry(pp, n_pairs, h->F, bins->n_par / bins->r_par_max,
+                                  bins->n_perp / bins->r_perp_max, cs, s),
+     "pair geometry");
+  st = run_xi(h, cat, 1, bins, prec, pp, cs, n_pairs, num, wsum, xi, s);
+  h->max_len = std::max(saved, ml);
+  return st;
+}
+
+int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_eta eta, double p_subsample,
+             uint64_t seed, double* dmat, double* wsum_dm, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!dmat) return fail(h, LYA_ERR_INVALID_ARG, "dmat is NULL");
+  if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
+    return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
+  if (eta != LYA_ETA_IDENTITY && eta != LYA_ETA_MEAN_SLOPE) return fail(h, LYA_ERR_INVALID_ARG, "eta");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  const int nb = bins->n_par * bins->n_perp;
+  const size_t gbytes = static_cast<size_t>(nb) * nb * 8 + static_cast<size_t>(nb) * 8;
+  cudaError_t e = grow(&h->gbuf, &h->g_cap, gbytes);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "D accumulator");
+  double* G = static_cast<double*>(h->gbuf);
+  double* wdm = G + static_cast<size_t>(nb) * nb;
+  DmArgs A;
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  A.eta_mean_slope = eta == LYA_ETA_MEAN_SLOPE ? 1 : 0;
+  A.p_subsample = p_subsample;
+  A.seed = seed;
+  A.G = G;
+  A.wdm = wdm;
+  A.max_len = h->max_len;
+  stage_begin(h, 1, s);
+  CK(run_dmat(A, h->dev, &h->scratch2, &h->scratch2_cap, s), "dmat");
+  stage_end(h, 1, s);
+  CK(launch_dm_finalize(G, wdm, dmat, wsum_dm, nb, s), "dmat finalize");
+  return LYA_OK;
+}
+
+int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* grad_xi,
+                    const double* xi, const double* wsum, float* grad_delta, float* grad_weight,
+                    void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!grad_xi || !xi || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "grad_xi/xi/wsum is NULL");
+  if (cat && cat->n_pix > 0 && (!grad_delta || !grad_weight))
+    return fail(h, LYA_ERR_INVALID_ARG, "gradient output is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  AdjArgs A;
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  A.grad_xi = grad_xi;
+  A.xi = xi;
+  A.wsum = wsum;
+  A.delta = cat->delta;
+  A.weight = cat->weight;
+  A.pix_base = 0;
+  A.n_pix = cat->n_pix;
+  A.grad_delta = grad_delta;
+  A.grad_weight = grad_weight;
+  A.max_len = h->max_len;
+  if (cat->n_pix > 0) {
+    CK(cudaMemsetAsync(grad_delta, 0, cat->n_pix * 4, s), "zero grad");
+    CK(cudaMemsetAsync(grad_weight, 0, cat->n_pix * 4, s), "zero grad");
+  }
+  stage_begin(h, 2, s);
+  CK(run_adjoint(A, h->dev, &h->scratch2, &h->scratch2_cap, s), "adjoint");
+  stage_end(h, 2, s);
+  return LYA_OK;
+}
+
+int lya_xi_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, const lya_bins* bins,
+                   lya_precision prec, double* num, double* wsum, double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (!mocks || n_mocks < 1) return fail(h, LYA_ERR_INVALID_ARG, "no mocks");
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!num && !wsum && !xi) return fail(h, LYA_ERR_INVALID_ARG, "no output requested");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, mocks, n_mocks, s);
+  if (st) return st;
+  st = ensure_pairs(h, mocks, n_mocks, bins, s);
+  if (st) return st;
+  return run_xi(h, mocks, n_mocks, bins, prec, static_cast<const int2*>(h->pairbuf),
+                static_cast<const float2*>(h->csbuf), h->n_pairs, num, wsum, xi, s);
+}
+
+int lya_autotune(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int32_t* choice,
+                 void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  // candidate (warps per block, pairs per work grab)
+  static const int cand[][2] = {{8, 1}, {8, 4}, {8, 16}, {4, 4}, {16, 4}, {12, 4}};
+  const int nc = sizeof(cand) / sizeof(cand[0]);
+  const int nb = bins->n_par * bins->n_perp;
+  cudaError_t e = grow(&h->outbuf, &h->out_cap, static_cast<size_t>(nb) * 16);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "output scratch");
+  double* N = static_cast<double*>(h->outbuf);
+  double* W = N + nb;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  int besti = 1;
+  for (int c = 0; c < nc; ++c) {
+    XiLaunch L;
+    if (plan_xi_mixed(h->dev, bins->n_par, h->max_len, cand[c][0], cand[c][1], &L) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    XiArgs A;
+    A.pairs = static_cast<const int2*>(h->pairbuf);
+    A.cs = static_cast<const float2*>(h->csbuf);
+    A.n_pairs = h->n_pairs;
+    A.pix = static_cast<const Pix*>(h->pixbuf);
+    A.F = h->F;
+    A.n_par = bins->n_par;
+    A.n_perp = bins->n_perp;
+    A.num = N;
+    A.wsum = W;
+    A.nb = nb;
+    A.counter = h->d_counter;
+    float tbest = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CK(cudaMemsetAsync(N, 0, nb * 16, s), "zero");
+      CK(cudaEventRecord(e0, s), "event");
+      CK(launch_xi_mixed(A, L, s), "xi kernel");
+      CK(cudaEventRecord(e1, s), "event");
+      CK(cudaEventSynchronize(e1), "event sync");
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tbest = std::min(tbest, ms);
+    }
+    if (tbest < best) {
+      best = tbest;
+      besti = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuned_warps = cand[besti][0];
+  h->tuned_grab = cand[besti][1];
+  h->tuned_for_npar = bins->n_par;
+  if (choice) *choice = besti;
+  return LYA_OK;
+}
+
+int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample,
+                   uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
+                   void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
+    return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  XiArgs A{};
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  StatsOut* dout = reinterpret_cast<StatsOut*>(h->d_u64 + 1);
+  CK(launch_pair_stats(A, p_subsample, seed, dout, h->dev, s), "pair stats");
+  StatsOut host{};
+  CK(cudaMemcpyAsync(&host, dout, sizeof(StatsOut), cudaMemcpyDeviceToHost, s), "read stats");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (n_pairs) *n_pairs = static_cast<int64_t>(host.pairs);
+  if (pixel_pairs) *pixel_pairs = static_cast<int64_t>(host.pix);
+  if (pixel_pairs_sq) *pixel_pairs_sq = static_cast<double>(host.pix_sq);
+  return LYA_OK;
+}
+
+int lya_stage_ms(lya_handle* h, int32_t stage, float* ms) {
+  if (!h || !ms || stage < 0 || stage > 3) return LYA_ERR_INVALID_ARG;
+  if (!h->ev_used[stage]) return fail(h, LYA_ERR_INVALID_ARG, "stage has not run");
+  CK(cudaEventSynchronize(h->ev[stage][1]), "event sync");
+  CK(cudaEventElapsedTime(ms, h->ev[stage][0], h->ev[stage][1]), "elapsed");
+  return LYA_OK;
+}
+
+int64_t lya_kernel_launches(void) { return static_cast<int64_t>(g_launches.load()); }
+
+int lya_last_launch(lya_handle* h, int64_t* n_pairs, int32_t* grid, int32_t* block, int32_t* smem_bytes) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  if (n_pairs) *n_pairs = h->last_pairs;
+  if (grid) *grid = h->last.blocks;
+  if (block) *block = h->last.warps * 32;
+  if (smem_bytes) *smem_bytes = h->last.smem;
+  return LYA_OK;
+}
+
+}  // extern "C"

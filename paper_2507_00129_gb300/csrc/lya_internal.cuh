@@ -1,0 +1,225 @@
+// Internal declarations shared by the CUDA translation units of liblya.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lya.h"
+
+namespace lya {
+
+// Device-side input-check flags (OR-ed into the handle's error word).
+enum : unsigned {
+  FLAG_UNSORTED = 1u,
+  FLAG_NONFINITE = 2u,
+  FLAG_OFFSETS = 4u,
+  FLAG_NEGATIVE_W = 8u,
+  FLAG_TOO_LONG = 16u,
+};
+
+// Per-forest data derived by the preparation kernel (structure of arrays).
+// Lengths of forests that fail the offset checks are set to 0 so that no
+// kernel ever reads outside the pixel arrays.
+struct Forests {
+  int64_t n;          // forests
+  int64_t* off;       // first pixel (global pixel index)
+  int32_t* len;       // pixel count (0 = ignored)
+  double* ux;         // unit vector of the line of sight
+  double* uy;
+  double* uz;
+  double* dmin;       // distance of the first pixel
+  double* dmax;       // distance of the last pixel
+  double* wsum;       // W = sum w
+  double* lbar;       // weighted mean of Lambda
+  double* ssum;       // S = sum w (Lambda - Lbar)^2
+  float* dref;        // reference distance, a multiple of 2^-10 (exact in FP32)
+  int32_t* mock;      // catalogue (mock) index of the forest
+};
+
+// Packed pixel record used by every FP32 kernel:
+//   x = fl32(d - dref), y = w, z = fl32(w * delta), w = fl32(Lambda - Lbar)
+using Pix = float4;
+
+// FP32 magic constant: fl_rd(x + 2^23) holds floor(x) in its low mantissa bits
+// for 0 <= x < 2^23.
+constexpr float kMagic = 8388608.0f;
+constexpr uint32_t kMagicBits = 0x4B000000u;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void red_add_f32_shared(uint32_t addr, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
+
+template <int OFF>
+__device__ __forceinline__ void red_add_f32_shared_off(uint32_t addr, float v) {
+  asm volatile("red.shared.add.f32 [%0+%2], %1;" ::"r"(addr), "f"(v), "n"(OFF));
+}
+
+__device__ __forceinline__ void red_add_f64_global(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// First output of the SplitMix64 generator (Steele, Lea, Flood 2014) for state x.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Subsample rule of the distortion matrix: keep forest pair (a, b) iff
+// all != 0 or SplitMix64(seed ^ (min(a,b) * 2^32 + max(a,b))) < thr.
+__device__ __forceinline__ bool keep_pair(int a, int b, uint64_t seed, uint64_t thr, int all) {
+  const uint64_t lo = static_cast<uint64_t>(min(a, b)), hi = static_cast<uint64_t>(max(a, b));
+  return all || (splitmix64(seed ^ ((lo << 32) | hi)) < thr);
+}
+
+// Number of elements of the sorted array a[0..n) strictly below v (v NaN -> n).
+__device__ __forceinline__ int count_below(const Pix* a, int n, float v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid].x < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files, called from api.cu)
+// ---------------------------------------------------------------------------
+struct DevInfo {
+  int sms;
+  int smem_optin;   // max dynamic shared memory per block (bytes)
+  int smem_per_sm;
+};
+
+// prep.cu
+// fp (optional) accumulates a 64-bit fingerprint of the catalogue geometry
+// (sum over forests of a hash of index, position, length and distance range).
+cudaError_t launch_prep(const lya_catalog& cat, int64_t forest_base, int64_t pix_base, int32_t mock,
+                        Forests F, Pix* pix, unsigned* err, unsigned long long* fp, cudaStream_t s);
+cudaError_t launch_project(const lya_catalog& cat, Forests F, int64_t forest_base, float* out,
+                           cudaStream_t s);
+cudaError_t launch_max_len(Forests F, int32_t* out, cudaStream_t s);
+
+// pairs.cu
+struct PairBuild {
+  int nside;
+  double rperp_max;
+  double theta_max;
+};
+// Builds the (a < b) pair list of forests [f0, f1) into *pairs (device buffer
+// grown with cudaMalloc as needed).  Synchronises.
+cudaError_t build_pairs(const Forests& F, int64_t f0, int64_t f1, const PairBuild& pb, int2** pairs,
+                        int64_t* cap, int64_t pair_base, int64_t* n_out, void** scratch,
+                        size_t* scratch_cap, cudaStream_t s);
+cudaError_t launch_pair_geometry(const int2* pairs, int64_t n, Forests F, double inv_dpar,
+                                 double inv_dperp, float2* cs, cudaStream_t s);
+cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int2* out,
+                              cudaStream_t s);
+cudaError_t launch_unpack_pairs(const int2* p, int64_t n, int32_t* a, int32_t* b, cudaStream_t s);
+
+// xi.cu
+struct XiLaunch {
+  int warps;       // warps per block
+  int blocks;      // persistent grid size
+  int hcap;        // histogram capacity (floats per array per warp)
+  int seg;         // pixel buffer per warp (pixels)
+  int grab;        // pairs per work grab
+  int smem;        // dynamic shared memory bytes
+};
+struct XiArgs {
+  const int2* pairs;
+  const float2* cs;
+  int64_t n_pairs;
+  const Pix* pix;
+  Forests F;
+  int n_par, n_perp;
+  double* num;
+  double* wsum;
+  int nb;
+  unsigned long long* counter;
+};
+cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps, int grab,
+                          XiLaunch* L);
+cudaError_t launch_xi_mixed(const XiArgs& a, const XiLaunch& L, cudaStream_t s);
+cudaError_t launch_xi_fp64(const XiArgs& a, const lya_catalog* cats, int n_cats, const DevInfo& dev,
+                           int max_len, double r_par_max, double r_perp_max, XiLaunch* used,
+                           cudaStream_t s);
+cudaError_t launch_finalize(const double* num, const double* wsum, double* xi, int64_t n,
+                            cudaStream_t s);
+
+// dmat.cu
+struct DmArgs {
+  const int2* pairs;
+  const float2* cs;
+  int64_t n_pairs;
+  const Pix* pix;
+  Forests F;
+  int n_par, n_perp;
+  int eta_mean_slope;
+  double p_subsample;
+  uint64_t seed;
+  double* G;        // [nb*nb] upper-triangle accumulator (A <= B)
+  double* wdm;      // [nb]
+  int max_len;
+};
+cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
+                     cudaStream_t s);
+cudaError_t launch_dm_finalize(const double* G, const double* wdm, double* D, double* wdm_out,
+                               int nb, cudaStream_t s);
+
+// adjoint.cu
+struct AdjArgs {
+  const int2* pairs;
+  const float2* cs;
+  int64_t n_pairs;
+  const Pix* pix;
+  Forests F;
+  int n_par, n_perp;
+  const double* grad_xi;
+  const double* xi;
+  const double* wsum;
+  const float* delta;   // caller's delta (for dL/dw = delta * ...)
+  const float* weight;
+  int64_t pix_base;
+  int64_t n_pix;
+  float* grad_delta;
+  float* grad_weight;
+  int max_len;
+};
+cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
+                        cudaStream_t s);
+
+// scratch helper (api.cu)
+cudaError_t grow(void** p, size_t* cap, size_t need);
+
+// process-wide count of kernel launches (api.cu); LYA_COUNT(n) adds n
+void count_launches(long long n);
+#define LYA_COUNT(n) ::lya::count_launches(n)
+
+// xi.cu: per-pair in-grid pixel-pair counts of the kept pairs
+struct StatsOut {
+  unsigned long long pairs;
+  unsigned long long pix;
+  unsigned long long pix_sq;
+};
+cudaError_t launch_pair_stats(const XiArgs& a, double p_subsample, uint64_t seed, StatsOut* out,
+                              const DevInfo& dev, cudaStream_t s);
+
+}  // namespace lya

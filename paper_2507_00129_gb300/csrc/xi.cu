@@ -1,0 +1,459 @@
+// Pixel-pair histogram of Eq. (2.4): for every forest pair (a, b) and every
+// pixel pair (i in a, j in b), bin (r_par, r_perp) and add (w d)_i (w d)_j and
+// w_i w_j to the bin (Section 2.1).
+//
+// Mixed kernel (LYA_PREC_MIXED), persistent, one forest pair per warp at a time:
+//  * forest b is staged in the warp's shared-memory buffer with coalesced
+//    16-byte loads; 32 pixels of forest a sit in registers (one per lane);
+//  * separations are FP32 fused multiply-adds on distances relative to a
+//    per-forest reference (multiple of 2^-10, so the reference differences and
+//    sums entering the pair constants are exact FP32 numbers):
+//        r_par/D  = | d~_j * (-c/D) + ((d~_i * c/D) + (ref_a - ref_b) c/D) |
+//        r_perp/D =   d~_j *   s/D  + ((d~_i * s/D) + (ref_a + ref_b) s/D)
+//  * floor() is an FP32 add rounded toward -inf of 2^23 (the integer lands in
+//    the low mantissa bits), so the bin index needs no float->int conversion;
+//  * the histogram is warp private and covers only the rows t of the pair's
+//    r_perp band (r_perp is monotone in both distances, so the band follows
+//    from the extreme pixels); products are FP32 and shared-memory float
+//    atomics accumulate one 32-pixel chunk of forest a (at most 32 x n_b
+//    terms per bin), which is then folded into a warp-private FP64 band
+//    accumulator; after the forest pair the FP64 band is added to the bin sums
+//    in global memory with FP64 atomics (skipping empty bins);
+//  * the j loop of each 32-pixel chunk of a is restricted to the pixels that
+//    can be in range (distances are sorted; two binary searches).
+// FP64 kernel (LYA_PREC_FP64): the same decomposition with FP64 distances,
+// separations, products and shared-memory sums, mirroring the oracle's
+// operation order: r = |d_i - d_j| * c, x = r * (1/D).
+#include <algorithm>
+#include <math.h>
+
+#include "lya_internal.cuh"
+
+namespace lya {
+namespace {
+
+constexpr int kHcap = 320;       // bins per histogram array per warp (mixed)
+constexpr int kHcap64 = 256;     // doubles per histogram array per warp (FP64)
+constexpr int kMaxSeg = 1024;    // pixel buffer cap per warp
+
+template <bool SINGLE>
+__device__ __forceinline__ void chunk_loop(const Pix* __restrict__ buf, int jlo, int jhi, float cp,
+                                           float sp, float uc, float us, float wdi, float wi,
+                                           float fnpar, float fnperp, uint32_t npar, uint32_t base,
+                                           uint32_t twin, uint32_t tspan) {
+#pragma unroll 4
+  for (int j = jlo; j < jhi; ++j) {
+    const Pix q = buf[j];
+    const float rp = fabsf(fmaf(-q.x, cp, uc));
+    const float rt = fmaf(q.x, sp, us);
+    const float pf = __fadd_rd(rp, kMagic);
+    const float tf = __fadd_rd(rt, kMagic);
+    const uint32_t idx = __float_as_uint(tf) * npar + __float_as_uint(pf);
+    const uint32_t addr = base + (idx << 2);
+    bool ok = (rp < fnpar) && (rt < fnperp);
+    if (!SINGLE) ok = ok && ((__float_as_uint(tf) - kMagicBits - twin) <= tspan);
+    if (ok) {
+      red_add_f32_shared(addr, wdi * q.z);
+      red_add_f32_shared_off<kHcap * 4>(addr, wi * q.y);
+    }
+  }
+}
+
+// FP32 chunk partials -> FP64 band accumulator (and clear the partials)
+__device__ __forceinline__ void fold_chunk(float* hN, double* aN, int Lw, int lane) {
+  float* hW = hN + kHcap;
+  double* aW = aN + kHcap;
+  __syncwarp();
+  for (int k = lane; k < Lw; k += 32) {
+    const float vw = hW[k], vn = hN[k];
+    if (vw != 0.f || vn != 0.f) {
+      aW[k] += static_cast<double>(vw);
+      aN[k] += static_cast<double>(vn);
+      hW[k] = 0.f;
+      hN[k] = 0.f;
+    }
+  }
+  __syncwarp();
+}
+
+__device__ void pair_mixed(const XiArgs& A, int a, int b, float cp, float sp, float* hN, uint32_t sN,
+                           double* aN, Pix* buf, int seg, int kmax, int lane) {
+  const int na = A.F.len[a], nb = A.F.len[b];
+  if (na == 0 || nb == 0) return;
+  const Pix* __restrict__ pa = A.pix + A.F.off[a];
+  const Pix* __restrict__ pb = A.pix + A.F.off[b];
+  const float refa = A.F.dref[a], refb = A.F.dref[b];
+  const float Dc = (refa - refb) * cp;
+  const float Ds = (refa + refb) * sp;
+  const int npar = A.n_par, nperp = A.n_perp;
+  const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(nperp);
+  const float da0 = pa[0].x, daL = pa[na - 1].x, db0 = pb[0].x, dbL = pb[nb - 1].x;
+  const float rt_min = fmaf(db0, sp, fmaf(da0, sp, Ds));
+  const float rt_max = fmaf(dbL, sp, fmaf(daL, sp, Ds));
+  if (!(rt_min < fnperp)) return;
+  const int t_lo = static_cast<int>(rt_min);
+  const int t_hi = (rt_max < fnperp) ? static_cast<int>(rt_max) : nperp - 1;
+  const int64_t out_off = static_cast<int64_t>(A.F.mock[a]) * A.nb;
+  double* aW = aN + kHcap;
+  for (int tw = t_lo; tw <= t_hi; tw += kmax) {
+    const int tw_hi = min(t_hi, tw + kmax - 1);
+    const int Lw = (tw_hi - tw + 1) * npar;
+    const bool single = (tw == t_lo) && (tw_hi == t_hi);
+    const uint32_t C = kMagicBits * static_cast<uint32_t>(npar + 1) +
+                       static_cast<uint32_t>(tw) * static_cast<uint32_t>(npar);
+    const uint32_t base = sN - 4u * C;
+    for (int j0 = 0; j0 < nb; j0 += seg) {
+      const int segn = min(seg, nb - j0);
+      __syncwarp();
+      for (int k = lane; k < segn; k += 32) buf[k] = pb[j0 + k];
+      __syncwarp();
+      for (int i0 = 0; i0 < na; i0 += 32) {
+        const int i = i0 + lane;
+        // lanes past the end carry a NaN distance: every range test fails for them
+        const Pix pi = (i < na) ? pa[i] : make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, 0.f);
+        const float uc = fmaf(pi.x, cp, Dc);
+        const float us = fmaf(pi.x, sp, Ds);
+        const int last = min(31, na - 1 - i0);
+        const float uc_first = __shfl_sync(0xffffffffu, uc, 0);
+        const float us_first = __shfl_sync(0xffffffffu, us, 0);
+        const float uc_last = __shfl_sync(0xffffffffu, uc, last);
+        float dlo = (uc_first - fnpar) / cp;
+        float dhi = (uc_last + fnpar) / cp;
+        if (sp > 0.f) dhi = fminf(dhi, (fnperp - us_first) / sp);
+        dlo -= fabsf(dlo) * 1e-5f + 1e-2f;
+        dhi += fabsf(dhi) * 1e-5f + 1e-2f;
+        const int jlo = count_below(buf, segn, dlo);
+        const int jhi = count_below(buf, segn, dhi);
+        if (jlo >= jhi) continue;
+        if (single)
+          chunk_loop<true>(buf, jlo, jhi, cp, sp, uc, us, pi.z, pi.y, fnpar, fnperp, npar, base, 0, 0);
+        else
+          chunk_loop<false>(buf, jlo, jhi, cp, sp, uc, us, pi.z, pi.y, fnpar, fnperp, npar, base,
+                            static_cast<uint32_t>(tw), static_cast<uint32_t>(tw_hi - tw));
+        fold_chunk(hN, aN, Lw, lane);
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < Lw; k += 32) {
+      const double vw = aW[k], vn = aN[k];
+      if (vw != 0.0 || vn != 0.0) {
+        const int tt = k / npar;
+        const int p = k - tt * npar;
+        const int64_t bin = out_off + static_cast<int64_t>(p) * nperp + tw + tt;
+        red_add_f64_global(A.wsum + bin, vw);
+        red_add_f64_global(A.num + bin, vn);
+        aW[k] = 0.0;
+        aN[k] = 0.0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(512) xi_mixed_kernel(XiArgs A, int seg, int kmax, int grab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per warp: FP64 band accumulator (2 x kHcap doubles), FP32 chunk
+  // histogram (2 x kHcap floats), pixel buffer (seg float4)
+  const int per_warp = kHcap * 16 + kHcap * 8 + seg * 16;
+  double* aN = reinterpret_cast<double*>(smem + wid * per_warp);
+  float* hN = reinterpret_cast<float*>(smem + wid * per_warp + kHcap * 16);
+  Pix* buf = reinterpret_cast<Pix*>(smem + wid * per_warp + kHcap * 24);
+  const uint32_t sN = smem_addr(hN);
+  for (int k = lane; k < 2 * kHcap; k += 32) {
+    hN[k] = 0.f;
+    aN[k] = 0.0;
+  }
+  __syncwarp();
+  for (;;) {
+    unsigned long long it0 = 0;
+    if (lane == 0) it0 = atomicAdd(A.counter, static_cast<unsigned long long>(grab));
+    it0 = __shfl_sync(0xffffffffu, it0, 0);
+    if (it0 >= static_cast<unsigned long long>(A.n_pairs)) break;
+    const int64_t it1 = min(static_cast<int64_t>(it0) + grab, A.n_pairs);
+    for (int64_t it = static_cast<int64_t>(it0); it < it1; ++it) {
+      const int2 ab = A.pairs[it];
+      if (ab.x < 0) continue;   // rejected pair
+      const float2 cs = A.cs[it];
+      pair_mixed(A, ab.x, ab.y, cs.x, cs.y, hN, sN, aN, buf, seg, kmax, lane);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// FP64 path
+// ----------------------------------------------------------------------------
+struct Fp64Args {
+  XiArgs A;
+  const double4_32a* pix64;   // {d, w, w*delta, 0}
+  double inv_dpar, inv_dperp;
+};
+
+__device__ __forceinline__ int count_below64(const double4_32a* a, int n, double v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid].x < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) xi_fp64_kernel(Fp64Args P, int seg, int kmax, int grab) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const XiArgs& A = P.A;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int per_warp = kHcap64 * 16 + seg * 32;
+  double* hN = reinterpret_cast<double*>(smem + wid * per_warp);
+  double* hW = hN + kHcap64;
+  double4_32a* buf = reinterpret_cast<double4_32a*>(smem + wid * per_warp + kHcap64 * 16);
+  for (int k = lane; k < 2 * kHcap64; k += 32) hN[k] = 0.0;
+  __syncwarp();
+  const int npar = A.n_par, nperp = A.n_perp;
+  const double fnpar = npar, fnperp = nperp;
+  for (;;) {
+    unsigned long long it0 = 0;
+    if (lane == 0) it0 = atomicAdd(A.counter, static_cast<unsigned long long>(grab));
+    it0 = __shfl_sync(0xffffffffu, it0, 0);
+    if (it0 >= static_cast<unsigned long long>(A.n_pairs)) break;
+    const int64_t it1 = min(static_cast<int64_t>(it0) + grab, A.n_pairs);
+    for (int64_t it = static_cast<int64_t>(it0); it < it1; ++it) {
+      const int2 ab = A.pairs[it];
+      if (ab.x < 0) continue;   // rejected pair
+      const int a = ab.x, b = ab.y;
+      const int na = A.F.len[a], nb = A.F.len[b];
+      if (na == 0 || nb == 0) continue;
+      const double4_32a* pa = P.pix64 + A.F.off[a];
+      const double4_32a* pb = P.pix64 + A.F.off[b];
+      const double sx = A.F.ux[a] + A.F.ux[b], sy = A.F.uy[a] + A.F.uy[b], sz = A.F.uz[a] + A.F.uz[b];
+      const double dx = A.F.ux[a] - A.F.ux[b], dy = A.F.uy[a] - A.F.uy[b], dz = A.F.uz[a] - A.F.uz[b];
+      const double c = 0.5 * sqrt(sx * sx + sy * sy + sz * sz);
+      const double s = 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
+      const double cp = c * P.inv_dpar, sp = s * P.inv_dperp;
+      const double rt_min = (pa[0].x + pb[0].x) * sp;
+      const double rt_max = (pa[na - 1].x + pb[nb - 1].x) * sp;
+      if (!(rt_min < fnperp)) continue;
+      const int t_lo = static_cast<int>(rt_min);
+      const int t_hi = (rt_max < fnperp) ? static_cast<int>(rt_max) : nperp - 1;
+      const int64_t out_off = static_cast<int64_t>(A.F.mock[a]) * A.nb;
+      for (int tw = t_lo; tw <= t_hi; tw += kmax) {
+        const int tw_hi = min(t_hi, tw + kmax - 1);
+        for (int j0 = 0; j0 < nb; j0 += seg) {
+          const int segn = min(seg, nb - j0);
+          __syncwarp();
+          for (int k = lane; k < segn; k += 32) buf[k] = pb[j0 + k];
+          __syncwarp();
+          for (int i0 = 0; i0 < na; i0 += 32) {
+            const int i = i0 + lane;
+            const double4_32a pi = (i < na) ? pa[i] : make_double4_32a(3.0e300, 0, 0, 0);
+            const int last = min(31, na - 1 - i0);
+            const double d_first = __shfl_sync(0xffffffffu, pi.x, 0);
+            const double d_last = __shfl_sync(0xffffffffu, pi.x, last);
+            double dlo = d_first - fnpar / cp;
+            double dhi = d_last + fnpar / cp;
+            if (sp > 0.0) dhi = fmin(dhi, fnperp / sp - d_first);
+            dlo -= fabs(dlo) * 1e-9 + 1e-6;
+            dhi += fabs(dhi) * 1e-9 + 1e-6;
+            const int jlo = count_below64(buf, segn, dlo);
+            const int jhi = count_below64(buf, segn, dhi);
+            for (int j = jlo; j < jhi; ++j) {
+              const double4_32a q = buf[j];
+              const double x = fabs(pi.x - q.x) * cp;
+              const double y = (pi.x + q.x) * sp;
+              if (x < fnpar && y < fnperp) {
+                const int p = static_cast<int>(x);
+                const int t = static_cast<int>(y);
+                if (t >= tw && t <= tw_hi) {
+                  const int k = (t - tw) * npar + p;
+                  atomicAdd(&hN[k], pi.z * q.z);
+                  atomicAdd(&hW[k], pi.y * q.y);
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();
+        const int Lw = (tw_hi - tw + 1) * npar;
+        for (int k = lane; k < Lw; k += 32) {
+          const double vw = hW[k], vn = hN[k];
+          if (vw != 0.0 || vn != 0.0) {
+            const int tt = k / npar;
+            const int p = k - tt * npar;
+            const int64_t bin = out_off + static_cast<int64_t>(p) * nperp + tw + tt;
+            red_add_f64_global(A.wsum + bin, vw);
+            red_add_f64_global(A.num + bin, vn);
+            hW[k] = 0.0;
+            hN[k] = 0.0;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+__global__ void pack64_kernel(lya_catalog cat, Forests F, int64_t forest_base, double4_32a* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = warp; f < cat.n_forests; f += nw) {
+    const int64_t gf = forest_base + f;
+    const int n = F.len[gf];
+    const int64_t o = cat.offsets[f];
+    const int64_t g = F.off[gf];
+    for (int k = lane; k < n; k += 32) {
+      const double w = cat.weight[o + k];
+      out[g + k] = make_double4_32a(cat.dist[o + k], w, w * static_cast<double>(cat.delta[o + k]), 0.0);
+    }
+  }
+}
+
+// In-grid pixel-pair count of every kept pair (same FP32 binning as the
+// mixed kernel); one warp per forest pair.
+__global__ void pair_stats_kernel(XiArgs A, uint64_t seed, uint64_t thr, int all, StatsOut* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float fnpar = static_cast<float>(A.n_par), fnperp = static_cast<float>(A.n_perp);
+  unsigned long long my_pairs = 0, my_pix = 0, my_sq = 0;
+  for (int64_t k = warp; k < A.n_pairs; k += nw) {
+    const int2 ab = A.pairs[k];
+    if (ab.x < 0 || !keep_pair(ab.x, ab.y, seed, thr, all)) continue;
+    const int na = A.F.len[ab.x], nb = A.F.len[ab.y];
+    const float cp = A.cs[k].x, sp = A.cs[k].y;
+    const float refa = A.F.dref[ab.x], refb = A.F.dref[ab.y];
+    const float Dc = (refa - refb) * cp, Ds = (refa + refb) * sp;
+    const Pix* pa = A.pix + A.F.off[ab.x];
+    const Pix* pb = A.pix + A.F.off[ab.y];
+    unsigned long long cnt = 0;
+    for (int i = lane; i < na; i += 32) {
+      const float di = pa[i].x;
+      const float uc = fmaf(di, cp, Dc), us = fmaf(di, sp, Ds);
+      for (int j = 0; j < nb; ++j) {
+        const float dj = pb[j].x;
+        const float rp = fabsf(fmaf(-dj, cp, uc));
+        const float rt = fmaf(dj, sp, us);
+        cnt += (rp < fnpar && rt < fnperp) ? 1ull : 0ull;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    my_pairs += 1;
+    my_pix += cnt;
+    my_sq += cnt * cnt;
+  }
+  if (lane == 0 && my_pairs) {
+    atomicAdd(&out->pairs, my_pairs);
+    atomicAdd(&out->pix, my_pix);
+    atomicAdd(&out->pix_sq, my_sq);
+  }
+}
+
+__global__ void finalize_kernel(const double* num, const double* wsum, double* xi, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double w = wsum[k];
+    xi[k] = (w != 0.0) ? num[k] / w : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps, int grab,
+                          XiLaunch* L) {
+  if (n_par > kHcap) return cudaErrorInvalidValue;
+  int seg = ((std::max(max_len, 1) + 31) / 32) * 32;
+  if (seg > kMaxSeg) seg = kMaxSeg;
+  L->warps = warps;
+  L->hcap = kHcap;
+  L->seg = seg;
+  L->grab = grab;
+  L->smem = warps * (kHcap * 24 + seg * 16);
+  if (L->smem > dev.smem_optin) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(xi_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       L->smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xi_mixed_kernel, warps * 32, L->smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidValue;
+  L->blocks = per_sm * dev.sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_xi_mixed(const XiArgs& a, const XiLaunch& L, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (a.n_pairs == 0) return cudaSuccess;
+  const int kmax = std::max(1, std::min(a.n_perp, kHcap / a.n_par));
+  LYA_COUNT(1), xi_mixed_kernel<<<L.blocks, L.warps * 32, L.smem, s>>>(a, L.seg, kmax, L.grab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xi_fp64(const XiArgs& a, const lya_catalog* cats, int n_cats, const DevInfo& dev,
+                           int max_len, double r_par_max, double r_perp_max, XiLaunch* used,
+                           cudaStream_t s) {
+  if (a.n_par > kHcap64) return cudaErrorInvalidValue;
+  // FP64 packed pixels, built on demand in a temporary buffer
+  int64_t npix = 0;
+  for (int m = 0; m < n_cats; ++m) npix += cats[m].n_pix;
+  double4_32a* pix64 = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&pix64), std::max<int64_t>(npix, 1) * 32, s);
+  if (e != cudaSuccess) return e;
+  int64_t fb = 0;
+  for (int m = 0; m < n_cats; ++m) {
+    if (cats[m].n_forests > 0) {
+      int64_t blocks = std::min<int64_t>((cats[m].n_forests * 32 + 255) / 256, 65535);
+      LYA_COUNT(1), pack64_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(cats[m], a.F, fb, pix64);
+    }
+    fb += cats[m].n_forests;
+  }
+  Fp64Args P;
+  P.A = a;
+  P.pix64 = pix64;
+  P.inv_dpar = static_cast<double>(a.n_par) / r_par_max;
+  P.inv_dperp = static_cast<double>(a.n_perp) / r_perp_max;
+  int seg = ((std::max(max_len, 1) + 31) / 32) * 32;
+  if (seg > 512) seg = 512;
+  const int warps = 4;
+  const int smem = warps * (kHcap64 * 16 + seg * 32);
+  e = cudaFuncSetAttribute(xi_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xi_fp64_kernel, warps * 32, smem);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
+  const int kmax = std::max(1, std::min(a.n_perp, kHcap64 / a.n_par));
+  if (e == cudaSuccess && a.n_pairs > 0) {
+    LYA_COUNT(1), xi_fp64_kernel<<<per_sm * dev.sms, warps * 32, smem, s>>>(P, seg, kmax, 4);
+    e = cudaGetLastError();
+  }
+  if (used) {
+    used->warps = warps;
+    used->blocks = per_sm * dev.sms;
+    used->seg = seg;
+    used->smem = smem;
+    used->hcap = kHcap64;
+    used->grab = 4;
+  }
+  cudaFreeAsync(pix64, s);
+  return e;
+}
+
+cudaError_t launch_pair_stats(const XiArgs& a, double p_subsample, uint64_t seed, StatsOut* out,
+                              const DevInfo& dev, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(StatsOut), s);
+  if (e != cudaSuccess || a.n_pairs == 0 || p_subsample <= 0.0) return e;
+  const int all = p_subsample >= 1.0 ? 1 : 0;
+  const uint64_t thr = all ? 0 : static_cast<uint64_t>(p_subsample * 18446744073709551616.0);
+  LYA_COUNT(1), pair_stats_kernel<<<dev.sms * 8, 256, 0, s>>>(a, seed, thr, all, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* num, const double* wsum, double* xi, int64_t n,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int64_t b = std::min<int64_t>((n + 255) / 256, 4096);
+  LYA_COUNT(1), finalize_kernel<<<static_cast<int>(b), 256, 0, s>>>(num, wsum, xi, n);
+  return cudaGetLastError();
+}
+
+}  // namespace lya
