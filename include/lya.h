@@ -207,6 +207,35 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
  * if the stage has not run on this handle. */
 int lya_stage_ms(lya_handle* h, int32_t stage, float* ms);
 
+/* The xi/W sums of lya_xi_pairs (MIXED precision) for callers that cannot
+ * allocate device memory.  The paper has no counterpart to this entry point.
+ *
+ * Who needs it: code that must not call cudaMalloc at run time -- for
+ * instance while another stream of the device is being captured into a CUDA
+ * graph in the global capture mode (cudaMalloc is refused there), inside a
+ * host whose device memory is entirely owned by a pool allocator, or in a
+ * real-time pipeline that reserves all memory at start-up.  It takes no
+ * handle (creating one allocates) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Scratch: one file-scope device array of this library, 38.5 MiB, held on
+ * every device where the library's module holding it is loaded (with CUDA's
+ * lazy module loading: from the first call of this function on that device)
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture begins.  Every call shares the array and leaves
+ * its contents behind; each call clears what must start at zero.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the array:
+ * serialise them.
+ *
+ * Limits: n_forests <= 65536, n_pix <= 1048576, n_pairs <= 1048576,
+ * n_par * n_perp <= 65536; beyond them LYA_ERR_TOO_LARGE is returned before
+ * any GPU work.  Arguments as for lya_xi_pairs (num/wsum may be NULL; xi needs
+ * neither).  Synchronises `stream` and returns the input-check status. */
+int lya_xi_pairs_static(const lya_catalog* cat, const lya_bins* bins, const int32_t* pair_a,
+                        const int32_t* pair_b, int64_t n_pairs, double* num, double* wsum, double* xi,
+                        void* stream);
+
 /* Number of CUDA kernels this library has launched in the calling process
  * since it was loaded (all handles).  Host-only; never fails. */
 int64_t lya_kernel_launches(void);

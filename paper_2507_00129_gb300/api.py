@@ -169,6 +169,22 @@ def lya_xi_pairs(handle: Handle, cat: DeviceCatalog, bins, pair_a: torch.Tensor,
     return num, wsum, xi
 
 
+def lya_xi_pairs_static(cat: DeviceCatalog, bins, pair_a: torch.Tensor, pair_b: torch.Tensor, stream=None):
+    """xi/W over explicit pairs using only the library's fixed device array
+    (no device allocation inside the library call; no handle)."""
+    nb = bins.n_par * bins.n_perp
+    num = torch.empty(nb, dtype=torch.float64, device="cuda")
+    wsum = torch.empty(nb, dtype=torch.float64, device="cuda")
+    xi = torch.empty(nb, dtype=torch.float64, device="cuda")
+    pa = pair_a.to(torch.int32).contiguous()
+    pb = pair_b.to(torch.int32).contiguous()
+    c, b = cat.c(), c_bins(bins)
+    check(None, _lib.load().lya_xi_pairs_static(ctypes.byref(c), ctypes.byref(b), _ptr(pa), _ptr(pb),
+                                                int(pa.numel()), _ptr(num), _ptr(wsum), _ptr(xi),
+                                                _stream(stream)))
+    return num, wsum, xi
+
+
 def lya_dmat(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed: int,
              eta: str = "mean_slope", stream=None):
     nb = bins.n_par * bins.n_perp
