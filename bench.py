@@ -134,6 +134,18 @@ def sum_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def rank_seed(rank: int) -> int:
+    """Catalogue seed of a rank: each rank runs its own independent mock."""
+    return 1 + rank
+
+
+def aggregate(ms_local: float, units_local: float, world: int):
+    """Whole-job timing over ranks: (max ms per step, total units, units/s)."""
+    ms = max_over_ranks(ms_local, world)
+    total = sum_over_ranks(units_local, world)
+    return ms, total, total / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle timing (the reported baseline and the reference arm)
 # ----------------------------------------------------------------------------
@@ -208,7 +220,12 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cat = synth.make(1, seed=1 + rank)
+    spec = synth.spec_for(1, seed=rank_seed(rank))
+    if args.forests:
+        # smaller catalogue at the same sky density (profiling captures)
+        spec.area_deg2 = spec.area_deg2 * args.forests / spec.n_forests
+        spec.n_forests = args.forests
+    cat = synth.generate(spec, name="sdss_like")
     bins = synth.bins_for(1)
     nb = bins.nbins
     dc = api.DeviceCatalog.from_host(cat, device=dev)
@@ -255,9 +272,7 @@ def run_ours(args, rank, world, local):
         barrier(world)
     launches = api.lya_kernel_launches() - launches0
     ms_local = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms_local, world)
-    pix_total = sum_over_ranks(float(st["pixel_pairs"]), world)
-    value = pix_total / (ms / 1e3)
+    ms, pix_total, value = aggregate(ms_local, float(st["pixel_pairs"]), world)
     med = {k: float(np.median(v)) for k, v in stage.items()}
 
     # end to end through the public API from pinned host memory
@@ -308,7 +323,8 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, l2="inputs larger than L2 (catalogue 450 MB; packed pixels 180 MB)",
+        "config": dict(WORKLOAD, **({"forests": args.forests} if args.forests else {}),
+                       l2="inputs larger than L2 (catalogue 450 MB; packed pixels 180 MB)",
                        step="project + pair list + xi/W mixed + D (5%) + adjoint",
                        seeds=f"catalogue seed 1+rank, DM seed {DM_SEED}"),
         "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
@@ -343,6 +359,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--forests", type=int, default=0,
+                    help="profiling: use this many forests (same sky density) instead of 60,000")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.impl == "reference":

@@ -119,7 +119,8 @@ int lya_sync_status(lya_handle* h, void* stream);
 int lya_pairs_build(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
                     int64_t* n_pairs, void* stream);
 
-/* Copy the cached pair list (sorted by (a, b)) into caller device arrays of
+/* Copy the cached pair list (each pair once with a < b, in the library's
+ * internal order: grouped by catalogue and first r_perp row) into caller device arrays of
  * capacity `cap`; *n_pairs (host) receives the count.  Synchronises.
  * Fails with LYA_ERR_INVALID_ARG if no list is cached or cap is too small. */
 int lya_pairs_get(lya_handle* h, int32_t* pair_a, int32_t* pair_b, int64_t cap,
@@ -218,7 +219,7 @@ int lya_stage_ms(lya_handle* h, int32_t stage, float* ms);
  * handle (creating one allocates) and calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *
- * Scratch: one file-scope device array of this library, 38.5 MiB, held on
+ * Scratch: one file-scope device array of this library, 39.3 MiB, held on
  * every device where the library's module holding it is loaded (with CUDA's
  * lazy module loading: from the first call of this function on that device)
  * until the process exits.  The first call on a device looks up the array's

@@ -193,7 +193,7 @@ int read_flags(lya_handle* h, cudaStream_t s, unsigned* out) {
 int ensure_workspace(lya_handle* h, int64_t nf, int64_t np) {
   if (nf > h->F_capacity || !h->fbuf) {
     const int64_t cap = std::max<int64_t>(nf, 1) + std::max<int64_t>(nf, 1) / 4;
-    const size_t bytes = static_cast<size_t>(cap) * (8 * 9 + 4 * 3) + 16 * 64;
+    const size_t bytes = static_cast<size_t>(cap) * (8 * 9 + 4 * 7) + 16 * 256;
     if (h->fbuf) { cudaDeviceSynchronize(); cudaFree(h->fbuf); h->fbuf = nullptr; }
     cudaError_t e = cudaMalloc(&h->fbuf, bytes);
     if (e != cudaSuccess) { h->F_capacity = 0; return fail(h, LYA_ERR_NO_MEMORY, "forest workspace"); }
@@ -212,6 +212,10 @@ int ensure_workspace(lya_handle* h, int64_t nf, int64_t np) {
     h->F.len = reinterpret_cast<int32_t*>(take(cap * 4));
     h->F.dref = reinterpret_cast<float*>(take(cap * 4));
     h->F.mock = reinterpret_cast<int32_t*>(take(cap * 4));
+    h->F.wmax = reinterpret_cast<float*>(take(cap * 4));
+    h->F.wdmax = reinterpret_cast<float*>(take(cap * 4));
+    h->F.hmin = reinterpret_cast<float*>(take(cap * 4));
+    h->F.xmax = reinterpret_cast<float*>(take(cap * 4));
     h->F_capacity = cap;
     h->pairs_valid = false;
   }
@@ -305,6 +309,9 @@ int build_all_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bin
   CK(launch_pair_geometry(pairs, total, h->F, b->n_par / b->r_par_max, b->n_perp / b->r_perp_max,
                           static_cast<float2*>(h->csbuf), s),
      "pair geometry");
+  CK(sort_pairs_by_band(pairs, static_cast<float2*>(h->csbuf), total, h->F, static_cast<const Pix*>(h->pixbuf),
+                        b->n_perp, n, &h->scratch, &h->scratch_cap, s),
+     "pair order");
   stage_end(h, 3, s);
   unsigned long long fp = 0;
   CK(cudaMemcpyAsync(&fp, h->d_fp, 8, cudaMemcpyDeviceToHost, s), "read fingerprint");

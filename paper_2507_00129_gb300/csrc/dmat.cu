@@ -18,14 +18,21 @@
 // kept pairs are grouped by (first band row, K); a block takes a chunk of
 // pairs of one group and keeps the upper triangle of the L x L block of D~
 // in shared memory (FP32), flushing it to the FP64 accumulator G (entries
-// A <= B) with FP64 atomics once per chunk.  Per pair and per batch of CB
-// columns (then rows): (a) every thread bins pixel pairs into dense per-column
-// histograms, (b) one warp per column compacts its histogram into a sorted
-// list of non-zero bins (and adds the column to the T vectors), (c) warps
-// apply the rank-1 updates of the lists to the triangle.  Pairs whose band is
-// too wide for shared memory take the same code with the triangle replaced by
-// FP64 atomics into G.  Binning uses exactly the FP32 arithmetic of the xi
-// kernel, so W^DM equals the xi weights of the kept pairs up to summation order.
+// A <= B) with FP64 atomics once per chunk.  The rank-1 terms are applied a
+// batch of up to CB vectors (consecutive columns, then rows) at a time:
+//  (a1) every thread bins pixel pairs and marks the local bins the batch
+//       touches; (b) one warp compacts the marks into the batch's sorted union
+//       support S (|S| is a little above one vector's support, because
+//       neighbouring columns visit nearly the same bins);
+//  (a2) the batch's histograms are summed densely on S with shared atomics;
+//       column histograms also feed the T vectors;
+//  (d)  each thread owns a 4 x 4 tile of the S x S upper triangle and adds
+//       sum_v (a_v a_v^T + b_v b_v^T) over the batch in registers (FP32 FMA,
+//       float4 loads), then updates its 16 triangle entries -- no atomics.
+// Pairs whose band is too wide for shared memory take the same code with the
+// triangle replaced by FP64 atomics into G.  Binning uses exactly the FP32
+// arithmetic of the xi kernel, so W^DM equals the xi weights of the kept
+// pairs up to summation order.
 #include <algorithm>
 #include <math.h>
 
@@ -37,14 +44,6 @@ namespace {
 constexpr int kDmThreads = 512;
 constexpr int kChunk = 128;
 
-struct DmPlan {
-  int kfit;      // largest band (rows) held in shared memory
-  int cb;        // columns per batch
-  int lcap;      // list capacity per column
-  int max_len;
-  int smem;      // bytes
-  int L;         // local bins allocated = kfit * n_par (or full band for wide)
-};
 
 // band of a pair: same FP32 arithmetic as the xi kernel
 __device__ __forceinline__ bool pair_band(const DmArgs& A, int a, int b, float sp, int* t_lo, int* K) {
@@ -123,12 +122,22 @@ __global__ void chunk_fill_kernel(const int32_t* count, const int64_t* start, co
   }
 }
 
+constexpr int kCB = 16;   // vectors per batch
+
 // Shared-memory layout of one block (offsets in bytes)
 struct Lay {
-  int U, Wacc, T4, dense, list, lcount, ucs, pixa, pixb, gbin, end;
+  int U, Wacc, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, gbin, misc, end;
 };
 
-__host__ __device__ inline Lay layout(int L, int cb, int lcap, int max_len, bool global_sink) {
+__host__ __device__ inline int scap_for(int L, int npar, int K) {
+  // union-support capacity: at least one vector's support bound 2 (n_par + K) + 2
+  int c = 2 * (npar + K) + 2;
+  c = c + c / 2;
+  if (c > L) c = L;
+  return (c + 3) & ~3;
+}
+
+__host__ __device__ inline Lay layout(int L, int scap, int max_len, bool global_sink) {
   auto al = [](int v) { return (v + 15) & ~15; };
   Lay y;
   int o = 0;
@@ -136,46 +145,47 @@ __host__ __device__ inline Lay layout(int L, int cb, int lcap, int max_len, bool
   if (!global_sink) o += al(static_cast<int>((static_cast<int64_t>(L) * (L + 1) / 2) * 4));
   y.Wacc = o; o += al(L * 4);
   y.T4 = o; o += al(L * 16);
-  y.dense = o; o += al(cb * L * 8);
-  y.list = o; o += al(cb * lcap * 16);
-  y.lcount = o; o += al(cb * 4);
+  y.Va = o; o += al(kCB * scap * 4);
+  y.Vb = o; o += al(kCB * scap * 4);
+  y.mark = o; o += al(L);
+  y.inv = o; o += al(L * 2);
+  y.S = o; o += al(scap * 4);
   y.ucs = o; o += al(max_len * 8);
   y.pixa = o; o += al(max_len * 16);
   y.pixb = o; o += al(max_len * 16);
+  y.tv = o; o += al(max_len * 8);
   y.gbin = o; o += al(L * 4);
+  y.misc = o; o += 64;
   y.end = o;
   return y;
 }
 
-struct Entry {
-  int32_t l;
-  float a;
-  float b;
-  float pad;
-};
-
-template <bool GLOBAL>
-__device__ __forceinline__ void sink_add(float* U, double* G, const int32_t* gbin, int nb, int r, int c,
-                                         int64_t rowbase, float v) {
-  if (!GLOBAL) {
-    atomicAdd(&U[rowbase + c], v);
-  } else {
-    const int A = gbin[r], B = gbin[c];
-    const int lo = min(A, B), hi = max(A, B);
-    red_add_f64_global(G + static_cast<int64_t>(lo) * nb + hi, static_cast<double>(v));
-  }
+__device__ __forceinline__ int tri_rowbase(int r, int L) {
+  // index of (r, c), c >= r, in the packed upper triangle is rowbase(r) + c
+  return r * (2 * L - r + 1) / 2 - r;
 }
 
-__device__ __forceinline__ int64_t tri_rowbase(int r, int L) {
-  // index of (r, c) for c >= r is rowbase(r) + c
-  return static_cast<int64_t>(r) * (2 * L - r + 1) / 2 - r;
+// Power of two sc = 2^(29 - e), 2^e <= B < 2^(e+1): sums bounded by B map below 2^30.
+__device__ __forceinline__ float word_scale(float B) {
+  if (!(B > 0.f) || !(B < 1e37f)) return 1.f;
+  const int e = static_cast<int>((__float_as_uint(B) >> 23) & 0xFFu) - 127;
+  return __uint_as_float(static_cast<uint32_t>(min(max(29 - e + 127, 1), 254)) << 23);
+}
+
+// Bin of pixel pair (i of a, j of b); returns the local bin or -1 if off-grid.
+__device__ __forceinline__ int local_bin(float2 u, float dj, float cp, float sp, float fnpar, float fnperp,
+                                         int npar, int t0) {
+  const float rp = fabsf(fmaf(-dj, cp, u.x));
+  const float rt = fmaf(dj, sp, u.y);
+  if (rp < fnpar && rt < fnperp) return (static_cast<int>(rt) - t0) * npar + static_cast<int>(rp);
+  return -1;
 }
 
 // One forest pair: accumulate its contribution into the triangle (or G).
 template <bool GLOBAL>
-__device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int cb, int lcap,
+__device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int scap,
                         unsigned char* sm, const Lay& y) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int2 pr = A.pairs[item];
   const float2 cs = A.cs[item];
   const int a = pr.x, b = pr.y;
@@ -194,13 +204,19 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int cb,
 
   float* U = reinterpret_cast<float*>(sm + y.U);
   float4* T4 = reinterpret_cast<float4*>(sm + y.T4);
-  float* dense = reinterpret_cast<float*>(sm + y.dense);
-  Entry* list = reinterpret_cast<Entry*>(sm + y.list);
-  int32_t* lcount = reinterpret_cast<int32_t*>(sm + y.lcount);
+  float* Va = reinterpret_cast<float*>(sm + y.Va);
+  float* Vb = reinterpret_cast<float*>(sm + y.Vb);
+  int32_t* Vai = reinterpret_cast<int32_t*>(sm + y.Va);   // same storage, fixed point while filling
+  int32_t* Vbi = reinterpret_cast<int32_t*>(sm + y.Vb);
+  int2* tv = reinterpret_cast<int2*>(sm + y.tv);
+  unsigned char* mark = sm + y.mark;
+  int16_t* inv = reinterpret_cast<int16_t*>(sm + y.inv);
+  int32_t* S = reinterpret_cast<int32_t*>(sm + y.S);
   float2* ucs = reinterpret_cast<float2*>(sm + y.ucs);
   Pix* pxa = reinterpret_cast<Pix*>(sm + y.pixa);
   Pix* pxb = reinterpret_cast<Pix*>(sm + y.pixb);
   const int32_t* gbin = reinterpret_cast<const int32_t*>(sm + y.gbin);
+  int* misc = reinterpret_cast<int*>(sm + y.misc);   // [0] = |S|
 
   const Pix* ga = A.pix + A.F.off[a];
   const Pix* gb = A.pix + A.F.off[b];
@@ -212,107 +228,182 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int cb,
   for (int k = tid; k < nb; k += blockDim.x) pxb[k] = gb[k];
   __syncthreads();
 
-  // two passes: side 0 = columns j of b (histograms over i of a),
-  //             side 1 = rows i of a (histograms over j of b)
+  // side 0: columns j of b (histograms over i of a, weights w_i, x_i)
+  // side 1: rows i of a (histograms over j of b, weights w_j, y_j)
   for (int side = 0; side < 2; ++side) {
     if (side == 1 && !eta) break;
     const int nvec = side == 0 ? nb : na;
     const int nother = side == 0 ? na : nb;
-    // coefficients of the rank-1 terms of this side
-    const double Wn = side == 0 ? Wa : Wb;   // normaliser of the summed-over forest
+    // rank-1 coefficients sqrt(w_v / W) and sqrt(w_v / S) of this side's
+    // vectors, from FP32 reciprocals computed once per pair (FP64 division is
+    // slow on this part)
+    const double Wn = side == 0 ? Wa : Wb;
     const double Sn = side == 0 ? Sa : Sb;
-    for (int v0 = 0; v0 < nvec; v0 += cb) {
+    const float inv_w = (eta && Wn > 0.0) ? static_cast<float>(1.0 / Wn) : 0.f;
+    const float inv_s = (eta && Sn > 0.0) ? static_cast<float>(1.0 / Sn) : 0.f;
+    // Histogram terms of the summed-over forest (w, w x) in fixed point, one
+    // 32-bit word each: shared memory adds integers natively.  A (vector, bin)
+    // sum holds at most 2 / (cp hmin) + 2 pixels (two windows of width 1/cp).
+    {
+      const int fs = side == 0 ? a : b;
+      const Pix* ps = side == 0 ? pxa : pxb;
+      const int ns_ = side == 0 ? na : nb;
+      const float nrun = 2.f / (cp * A.F.hmin[fs]) + 2.f;
+      const float scA = word_scale(nrun * A.F.wmax[fs]);
+      const float scB = word_scale(nrun * A.F.wmax[fs] * A.F.xmax[fs]);
+      if (tid == 0) {
+        reinterpret_cast<float*>(misc)[1] = 1.f / scA;
+        reinterpret_cast<float*>(misc)[2] = 1.f / scB;
+      }
+      for (int k = tid; k < ns_; k += blockDim.x)
+        tv[k] = make_int2(__float2int_rn(ps[k].y * scA), __float2int_rn(ps[k].y * ps[k].w * scB));
+      __syncthreads();
+    }
+    const float inv_scA = reinterpret_cast<float*>(misc)[1];
+    const float inv_scB = reinterpret_cast<float*>(misc)[2];
+    int v0 = 0;
+    int cb = kCB;
+    while (v0 < nvec) {
       const int cbn = min(cb, nvec - v0);
-      // (a) dense histograms: thread -> (vector vv = tid % cb, partners o)
-      const int vv_t = tid % cb;
-      const int ostep = blockDim.x / cb;
-      for (int o = tid / cb; o < nother && vv_t < cbn; o += ostep) {
-        const int vv = vv_t;
-        const int i = side == 0 ? o : v0 + vv;   // pixel of a
-        const int j = side == 0 ? v0 + vv : o;   // pixel of b
-        const float2 u = ucs[i];
-        const float dj = pxb[j].x;
-        const float rp = fabsf(fmaf(-dj, cp, u.x));
-        const float rt = fmaf(dj, sp, u.y);
-        if (rp < fnpar && rt < fnperp) {
-          const int p = static_cast<int>(rp);
-          const int t = static_cast<int>(rt);
-          const int l = (t - t0) * npar + p;
-          // summed-over pixel: i of a (side 0) or j of b (side 1)
-          const Pix q = side == 0 ? pxa[i] : pxb[j];
-          atomicAdd(&dense[(vv * L + l) * 2 + 0], q.y);
-          atomicAdd(&dense[(vv * L + l) * 2 + 1], q.y * q.w);
-        }
+      // (a1) mark the local bins the batch touches
+      const int vv_t = tid % cbn;
+      const int ostep = blockDim.x / cbn;
+      for (int o = tid / cbn; o < nother && tid < ostep * cbn; o += ostep) {
+        const int i = side == 0 ? o : v0 + vv_t;
+        const int j = side == 0 ? v0 + vv_t : o;
+        const int l = local_bin(ucs[i], pxb[j].x, cp, sp, fnpar, fnperp, npar, t0);
+        if (l >= 0) mark[l] = 1;
       }
       __syncthreads();
-      // (b) compaction, one warp per vector
-      for (int vv = wid; vv < cbn; vv += nwarps) {
-        const Pix me = side == 0 ? pxb[v0 + vv] : pxa[v0 + vv];   // the vector's own pixel
-        const float wv = me.y;
-        const float ca = (eta && Wn > 0.0) ? sqrtf(static_cast<float>(wv / Wn)) : 0.f;
-        const float cbeta = (eta && Sn > 0.0) ? sqrtf(static_cast<float>(wv / Sn)) : 0.f;
+      // (b) compaction of the marks into S, inverse map; everyone else clears V
+      if (wid == 0) {
         int m = 0;
         for (int l0 = 0; l0 < L; l0 += 32) {
           const int l = l0 + lane;
-          float va = 0.f, vb = 0.f;
-          if (l < L) {
-            va = dense[(vv * L + l) * 2 + 0];
-            vb = dense[(vv * L + l) * 2 + 1];
-          }
-          const bool nz = (va != 0.f) || (vb != 0.f);
-          const unsigned msk = __ballot_sync(0xffffffffu, nz);
-          if (nz) {
+          const bool on = (l < L) && mark[l];
+          const unsigned msk = __ballot_sync(0xffffffffu, on);
+          if (on) {
             const int pos = m + __popc(msk & ((1u << lane) - 1u));
-            if (pos < lcap) {
-              Entry e;
-              e.l = l;
-              e.a = va * ca;
-              e.b = vb * cbeta;
-              e.pad = 0.f;
-              list[vv * lcap + pos] = e;
-            }
-            dense[(vv * L + l) * 2 + 0] = 0.f;
-            dense[(vv * L + l) * 2 + 1] = 0.f;
-            if (side == 0) {
-              // T vectors from the column histograms of b's pixel j = v0 + vv
-              const float wj = wv, yj = me.w;
-              atomicAdd(&T4[l].x, wj * va);
-              atomicAdd(&T4[l].y, wj * vb);
-              atomicAdd(&T4[l].z, wj * yj * va);
-              atomicAdd(&T4[l].w, wj * yj * vb);
-            }
+            if (pos < scap) S[pos] = l;
+            inv[l] = static_cast<int16_t>(pos);
+            mark[l] = 0;
           }
           m += __popc(msk);
         }
-        if (lane == 0) lcount[vv] = min(m, lcap);
+        if (lane == 0) misc[0] = m;
+      } else {
+        for (int k = tid - 32; k < kCB * scap; k += blockDim.x - 32) {
+          Va[k] = 0.f;
+          Vb[k] = 0.f;
+        }
       }
       __syncthreads();
-      // (c) rank-1 updates: warps split over vectors and over k
+      const int ns = misc[0];
+      if (ns > scap) {
+        // union too large for the staging arrays: retry with half the batch
+        __syncthreads();
+        cb = max(1, cbn / 2);
+        continue;
+      }
+      // (a2) dense histograms on S
+      for (int o = tid / cbn; o < nother && tid < ostep * cbn; o += ostep) {
+        const int i = side == 0 ? o : v0 + vv_t;
+        const int j = side == 0 ? v0 + vv_t : o;
+        const int l = local_bin(ucs[i], pxb[j].x, cp, sp, fnpar, fnperp, npar, t0);
+        if (l >= 0) {
+          const int2 t = tv[side == 0 ? i : j];   // the summed-over pixel's terms
+          const int k = vv_t * scap + inv[l];
+          atomicAdd(reinterpret_cast<unsigned*>(&Vai[k]), static_cast<unsigned>(t.x));
+          atomicAdd(reinterpret_cast<unsigned*>(&Vbi[k]), static_cast<unsigned>(t.y));
+        }
+      }
+      __syncthreads();
+      // T vectors (from unscaled column histograms) and scaling by the
+      // rank-1 coefficients sqrt(w_v / W), sqrt(w_v / S)
+      for (int k = tid; k < ns; k += blockDim.x) {
+        float t1 = 0.f, tx = 0.f, ty = 0.f, txy = 0.f;
+        for (int vv = 0; vv < cbn; ++vv) {
+          const Pix me = side == 0 ? pxb[v0 + vv] : pxa[v0 + vv];
+          const float va = static_cast<float>(Vai[vv * scap + k]) * inv_scA;
+          const float vb = static_cast<float>(Vbi[vv * scap + k]) * inv_scB;
+          if (side == 0) {
+            t1 = fmaf(me.y, va, t1);
+            tx = fmaf(me.y, vb, tx);
+            ty = fmaf(me.y * me.w, va, ty);
+            txy = fmaf(me.y * me.w, vb, txy);
+          }
+          const float ca = sqrtf(me.y * inv_w);
+          const float cbeta = sqrtf(me.y * inv_s);
+          Va[vv * scap + k] = va * ca;
+          Vb[vv * scap + k] = vb * cbeta;
+        }
+        if (side == 0) {
+          float4 t = T4[S[k]];
+          t.x += t1;
+          t.y += tx;
+          t.z += ty;
+          t.w += txy;
+          T4[S[k]] = t;
+        }
+      }
+      __syncthreads();
+      // (d) rank-1 updates of the batch: 4 x 4 register tiles of S x S
       if (eta) {
-        const int per = max(1, nwarps / max(cbn, 1));
-        for (int w = wid; w < cbn * per; w += nwarps) {
-          const int vv = w % cbn;
-          const int part = w / cbn;
-          const int m = lcount[vv];
-          const Entry* li = list + vv * lcap;
-          for (int k = lane + 32 * part; k < m; k += 32 * per) {
-            const Entry ek = li[k];
-            const int64_t rb = tri_rowbase(ek.l, L);
-            for (int l = k; l < m; ++l) {
-              const Entry el = li[l];
-              const float v = -(ek.a * el.a + ek.b * el.b);
-              sink_add<GLOBAL>(U, A.G, gbin, nbins, ek.l, el.l, rb, v);
+        const int nt = (ns + 3) >> 2;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int q = tid; q < ntiles; q += blockDim.x) {
+          int rr = static_cast<int>((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+          while (rr * (rr + 1) / 2 > q) --rr;
+          while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
+          const int cblk = rr;                      // column block (>= row block)
+          const int rblk = q - rr * (rr + 1) / 2;   // row block
+          float acc[4][4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+          for (int vv = 0; vv < cbn; ++vv) {
+            const float4 ar = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * rblk);
+            const float4 ac = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * cblk);
+            const float4 br = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * rblk);
+            const float4 bc = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * cblk);
+            const float arv[4] = {ar.x, ar.y, ar.z, ar.w}, acv[4] = {ac.x, ac.y, ac.z, ac.w};
+            const float brv[4] = {br.x, br.y, br.z, br.w}, bcv[4] = {bc.x, bc.y, bc.z, bc.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(brv[u], bcv[v], fmaf(arv[u], acv[v], acc[u][v]));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * rblk + u;
+            if (r >= ns) continue;
+            const int lr = S[r];
+            const int rb = tri_rowbase(lr, L);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int c = 4 * cblk + v;
+              if (c >= ns || c < r) continue;
+              const int lc = S[c];
+              if (!GLOBAL) {
+                U[rb + lc] -= acc[u][v];
+              } else {
+                const int Ar = gbin[lr], Ac = gbin[lc];
+                red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+                                   -static_cast<double>(acc[u][v]));
+              }
             }
           }
         }
       }
-      // the next batch's (a) writes only dense (already cleared); its barrier
-      // separates these list reads from the next (b)
+      __syncthreads();
+      v0 += cbn;
+      cb = kCB;
     }
-    __syncthreads();
   }
 
   // T terms, diagonal and W: one warp per row r, lanes over c >= r
+  const int nwarps = blockDim.x >> 5;
   const float c11 = (eta && Wa > 0 && Wb > 0) ? static_cast<float>(1.0 / (Wa * Wb)) : 0.f;
   const float cyy = (eta && Wa > 0 && Sb > 0) ? static_cast<float>(1.0 / (Wa * Sb)) : 0.f;
   const float cxx = (eta && Sa > 0 && Wb > 0) ? static_cast<float>(1.0 / (Sa * Wb)) : 0.f;
@@ -322,14 +413,19 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int cb,
     const float4 tr = T4[r];
     if (tr.x == 0.f && tr.y == 0.f && tr.z == 0.f && tr.w == 0.f) continue;
     const float f1 = c11 * tr.x, fy = cyy * tr.z, fx = cxx * tr.y, fxy = cxy * tr.w;
-    const int64_t rb = tri_rowbase(r, L);
+    const int rb = tri_rowbase(r, L);
     for (int c = r + lane; c < L; c += 32) {
       const float4 tc = T4[c];
       float v = f1 * tc.x + fy * tc.z + fx * tc.y + fxy * tc.w;
       if (c == r) v += tr.x;
       if (v != 0.f) {
-        if (!GLOBAL) U[rb + c] += v;   // (r, c) owned by this lane
-        else sink_add<true>(U, A.G, gbin, nbins, r, c, rb, v);
+        if (!GLOBAL) {
+          U[rb + c] += v;   // (r, c) owned by this lane
+        } else {
+          const int Ar = gbin[r], Ac = gbin[c];
+          red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+                             static_cast<double>(v));
+        }
       }
     }
     if (lane == 0) {
@@ -346,29 +442,29 @@ template <bool GLOBAL>
 __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk* chunks,
                                                            const int32_t* n_chunks_dev,
                                                            const int32_t* order, const int32_t* wide,
-                                                           const int32_t* n_wide_dev, int cb, int lcap,
-                                                           int Lalloc, unsigned long long* counter) {
+                                                           const int32_t* n_wide_dev, int scap, int Lalloc,
+                                                           unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_item;
   const int tid = threadIdx.x;
   const int nbins = A.n_par * A.n_perp;
   const int n_items = GLOBAL ? *n_wide_dev : *n_chunks_dev;
-  const Lay y = layout(Lalloc, cb, lcap, A.max_len, GLOBAL);
+  const Lay y = layout(Lalloc, scap, A.max_len, GLOBAL);
   float* U = reinterpret_cast<float*>(sm + y.U);
   float* Wacc = reinterpret_cast<float*>(sm + y.Wacc);
-  float* dense = reinterpret_cast<float*>(sm + y.dense);
   float4* T4 = reinterpret_cast<float4*>(sm + y.T4);
+  unsigned char* mark = sm + y.mark;
   int32_t* gbin = reinterpret_cast<int32_t*>(sm + y.gbin);
   // clear all accumulators once
   if (!GLOBAL) {
-    const int64_t nt = static_cast<int64_t>(Lalloc) * (Lalloc + 1) / 2;
-    for (int64_t k = tid; k < nt; k += blockDim.x) U[k] = 0.f;
+    const int nt = Lalloc * (Lalloc + 1) / 2;
+    for (int k = tid; k < nt; k += blockDim.x) U[k] = 0.f;
   }
   for (int k = tid; k < Lalloc; k += blockDim.x) {
     Wacc[k] = 0.f;
     T4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    mark[k] = 0;
   }
-  for (int k = tid; k < cb * Lalloc * 2; k += blockDim.x) dense[k] = 0.f;
   __syncthreads();
   for (;;) {
     if (tid == 0) s_item = static_cast<long long>(atomicAdd(counter, 1ull));
@@ -394,14 +490,13 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     __syncthreads();
     for (int q = 0; q < cnt; ++q) {
       const int pi = GLOBAL ? wide[item] : order[first + q];
-      dm_pair<GLOBAL>(A, pi, t0, K, L, cb, lcap, sm, y);
+      dm_pair<GLOBAL>(A, pi, t0, K, L, scap, sm, y);
     }
     if (!GLOBAL) {
       // flush the triangle and W of this chunk
-      const int64_t nt = static_cast<int64_t>(L) * (L + 1) / 2;
       const int nwarps = blockDim.x >> 5, wid = tid >> 5, lane = tid & 31;
       for (int r = wid; r < L; r += nwarps) {
-        const int64_t rb = tri_rowbase(r, L);
+        const int rb = tri_rowbase(r, L);
         const int Ar = gbin[r];
         for (int c = r + lane; c < L; c += 32) {
           const float v = U[rb + c];
@@ -419,7 +514,6 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
           Wacc[k] = 0.f;
         }
       }
-      (void)nt;
       __syncthreads();
     }
   }
@@ -488,22 +582,24 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   const int nbins = a.n_par * a.n_perp;
   const int max_len = std::max(a.max_len, 1);
   // largest band that fits in shared memory
-  int cb = 8, kfit = 0, lcap = 0;
+  int kfit = 0, scap = 0;
   for (int K = a.n_perp; K >= 1; --K) {
     const int L = K * a.n_par;
-    const int lc = std::min(L, 2 * (a.n_par + K) + 2);
-    const Lay y = layout(L, cb, lc, max_len, false);
-    if (y.end + 64 <= dev.smem_optin) {
+    const int sc = scap_for(L, a.n_par, K);
+    if (layout(L, sc, max_len, false).end + 64 <= dev.smem_optin) {
       kfit = K;
-      lcap = lc;
+      scap = sc;
       break;
     }
   }
   // wide-pair configuration (triangle in global memory)
-  int cbw = 8, Lw = a.n_perp * a.n_par, lcapw = std::min(Lw, 2 * (a.n_par + a.n_perp) + 2);
-  while (cbw > 1 && layout(Lw, cbw, lcapw, max_len, true).end + 64 > dev.smem_optin) cbw >>= 1;
-  if (layout(Lw, cbw, lcapw, max_len, true).end + 64 > dev.smem_optin) return cudaErrorInvalidValue;
-  if (kfit == 0) kfit = 1;  // everything goes wide
+  const int Lw = a.n_perp * a.n_par;
+  const int scapw = scap_for(Lw, a.n_par, a.n_perp);
+  if (layout(Lw, scapw, max_len, true).end + 64 > dev.smem_optin) return cudaErrorInvalidValue;
+  if (kfit == 0) {  // everything goes wide
+    kfit = 1;
+    scap = scap_for(a.n_par, a.n_par, 1);
+  }
 
   const int ngroups = a.n_perp * kfit;
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
@@ -555,20 +651,20 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   // main launch: shared-memory triangle
   {
     const int L = kfit * a.n_par;
-    const Lay y = layout(L, cb, lcap, max_len, false);
+    const Lay y = layout(L, scap, max_len, false);
     LYA_TRY(cudaFuncSetAttribute(dm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc, cb,
-                                                        lcap, L, counter);
+    LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
+                                                                      scap, L, counter);
     LYA_TRY(cudaGetLastError());
   }
   // wide pairs
   {
-    const Lay y = layout(Lw, cbw, lcapw, max_len, true);
+    const Lay y = layout(Lw, scapw, max_len, true);
     LYA_TRY(cudaFuncSetAttribute(dm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc, cbw,
-                                                       lcapw, Lw, counter);
+    LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
+                                                                     scapw, Lw, counter);
     LYA_TRY(cudaGetLastError());
   }
   return cudaSuccess;

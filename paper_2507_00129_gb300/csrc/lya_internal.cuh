@@ -34,6 +34,10 @@ struct Forests {
   double* ssum;       // S = sum w (Lambda - Lbar)^2
   float* dref;        // reference distance, a multiple of 2^-10 (exact in FP32)
   int32_t* mock;      // catalogue (mock) index of the forest
+  float* wmax;        // largest weight of the forest
+  float* wdmax;       // largest |w delta| of the forest
+  float* hmin;        // smallest gap between consecutive packed distances (> 0)
+  float* xmax;        // largest |Lambda - Lbar| of the forest
 };
 
 // Packed pixel record used by every FP32 kernel:
@@ -132,6 +136,10 @@ cudaError_t launch_pair_geometry(const int2* pairs, int64_t n, Forests F, double
                                  double inv_dperp, float2* cs, cudaStream_t s);
 cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int2* out,
                               cudaStream_t s);
+// Reorder pairs (and their geometry) by (mock, first r_perp row of the band)
+// so that consecutive pairs share the pair kernel's accumulator.
+cudaError_t sort_pairs_by_band(int2* pairs, float2* cs, int64_t n, Forests F, const Pix* pix, int n_perp,
+                               int n_mocks, void** scratch, size_t* scratch_cap, cudaStream_t s);
 cudaError_t launch_unpack_pairs(const int2* p, int64_t n, int32_t* a, int32_t* b, cudaStream_t s);
 
 // xi.cu

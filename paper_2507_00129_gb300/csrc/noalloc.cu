@@ -22,8 +22,8 @@ constexpr int64_t kStaticBins = 65536;
 constexpr size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // byte offsets inside the static array
-constexpr size_t kOffForest = 0;                                      // 12 arrays of kStaticForests
-constexpr size_t kForestBytes = al256(kStaticForests * 8) * 9 + al256(kStaticForests * 4) * 3;
+constexpr size_t kOffForest = 0;                                      // 16 arrays of kStaticForests
+constexpr size_t kForestBytes = al256(kStaticForests * 8) * 9 + al256(kStaticForests * 4) * 7;
 constexpr size_t kOffPix = kOffForest + kForestBytes;                  // float4 pixels
 constexpr size_t kOffPairs = kOffPix + al256(kStaticPix * 16);         // int2 pairs
 constexpr size_t kOffCs = kOffPairs + al256(kStaticPairs * 8);         // float2 pair geometry
@@ -114,6 +114,10 @@ extern "C" int lya_xi_pairs_static(const lya_catalog* cat, const lya_bins* bins,
     F.len = reinterpret_cast<int32_t*>(take(kStaticForests * 4));
     F.dref = reinterpret_cast<float*>(take(kStaticForests * 4));
     F.mock = reinterpret_cast<int32_t*>(take(kStaticForests * 4));
+    F.wmax = reinterpret_cast<float*>(take(kStaticForests * 4));
+    F.wdmax = reinterpret_cast<float*>(take(kStaticForests * 4));
+    F.hmin = reinterpret_cast<float*>(take(kStaticForests * 4));
+    F.xmax = reinterpret_cast<float*>(take(kStaticForests * 4));
   }
   Pix* pix = reinterpret_cast<Pix*>(base + kOffPix);
   int2* pairs = reinterpret_cast<int2*>(base + kOffPairs);

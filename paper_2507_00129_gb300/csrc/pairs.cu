@@ -323,6 +323,40 @@ __global__ void unpack_pairs_kernel(const int2* p, int64_t n, int32_t* a, int32_
   }
 }
 
+// key = mock * (n_perp + 1) + first r_perp row of the pair's band (n_perp if
+// the pair has nothing in the grid); same FP32 arithmetic as the pair kernel
+__global__ void band_key_kernel(const int2* pairs, const float2* cs, int64_t n, Forests F, const Pix* pix,
+                                int n_perp, int32_t* key, int32_t* count) {
+  const float fnperp = static_cast<float>(n_perp);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 p = pairs[k];
+    int t = n_perp;
+    const int na = F.len[p.x], nb = F.len[p.y];
+    if (na > 0 && nb > 0) {
+      const float sp = cs[k].y;
+      const float Ds = (F.dref[p.x] + F.dref[p.y]) * sp;
+      const float rt_min = fmaf(pix[F.off[p.y]].x, sp, fmaf(pix[F.off[p.x]].x, sp, Ds));
+      if (rt_min < fnperp) t = static_cast<int>(rt_min);
+    }
+    const int kk = F.mock[p.x] * (n_perp + 1) + t;
+    key[k] = kk;
+    atomicAdd(&count[kk], 1);
+  }
+}
+
+__global__ void band_scatter_kernel(const int2* pairs, const float2* cs, int64_t n, const int32_t* key,
+                                    const int64_t* start, int32_t* cursor, int2* pairs_out,
+                                    float2* cs_out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t kk = key[k];
+    const int64_t pos = start[kk] + atomicAdd(&cursor[kk], 1);
+    pairs_out[pos] = pairs[k];
+    cs_out[pos] = cs[k];
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -457,6 +491,37 @@ cudaError_t launch_pair_geometry(const int2* pairs, int64_t n, Forests F, double
   if (n == 0) return cudaSuccess;
   LYA_COUNT(1), pair_geometry_kernel<<<grid_for(n, kT), kT, 0, s>>>(pairs, n, F, inv_dpar, inv_dperp, cs);
   return cudaGetLastError();
+}
+
+cudaError_t sort_pairs_by_band(int2* pairs, float2* cs, int64_t n, Forests F, const Pix* pix, int n_perp,
+                               int n_mocks, void** scratch, size_t* scratch_cap, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  const int64_t nkeys = static_cast<int64_t>(n_mocks) * (n_perp + 1);
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t o_key = 0;
+  const size_t o_count = o_key + al(n * 4);
+  const size_t o_cursor = o_count + al(nkeys * 4);
+  const size_t o_start = o_cursor + al(nkeys * 4);
+  const size_t o_pairs = o_start + al((nkeys + 1) * 8);
+  const size_t o_cs = o_pairs + al(n * 8);
+  const size_t o_end = o_cs + al(n * 8);
+  LYA_TRY(grow(scratch, scratch_cap, o_end));
+  char* sc = static_cast<char*>(*scratch);
+  int32_t* key = reinterpret_cast<int32_t*>(sc + o_key);
+  int32_t* count = reinterpret_cast<int32_t*>(sc + o_count);
+  int32_t* cursor = reinterpret_cast<int32_t*>(sc + o_cursor);
+  int64_t* start = reinterpret_cast<int64_t*>(sc + o_start);
+  int2* p2 = reinterpret_cast<int2*>(sc + o_pairs);
+  float2* c2 = reinterpret_cast<float2*>(sc + o_cs);
+  LYA_TRY(cudaMemsetAsync(count, 0, nkeys * 4, s));
+  LYA_TRY(cudaMemsetAsync(cursor, 0, nkeys * 4, s));
+  LYA_COUNT(1), band_key_kernel<<<grid_for(n, kT), kT, 0, s>>>(pairs, cs, n, F, pix, n_perp, key, count);
+  LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(count, nkeys, start);
+  LYA_COUNT(1), band_scatter_kernel<<<grid_for(n, kT), kT, 0, s>>>(pairs, cs, n, key, start, cursor, p2, c2);
+  LYA_TRY(cudaGetLastError());
+  LYA_TRY(cudaMemcpyAsync(pairs, p2, n * 8, cudaMemcpyDeviceToDevice, s));
+  LYA_TRY(cudaMemcpyAsync(cs, c2, n * 8, cudaMemcpyDeviceToDevice, s));
+  return cudaSuccess;
 }
 
 cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int2* out,

@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(lya_catalog cat, int
     // so that differences and sums of two references are exact FP32 values).
     const float dref_f = (n > 0 && isfinite(d0)) ? static_cast<float>(floor(d0 * 1024.0) / 1024.0) : 0.0f;
     const double dref = static_cast<double>(dref_f);
-    // pass 2: slope normaliser and packed pixels
+    // pass 2: slope normaliser, packed pixels, bounds used for fixed-point scaling
     double ss = 0.0;
+    float wmx = 0.f, wdmx = 0.f, hmn = INFINITY, xmx = 0.f;
     for (int64_t k = lane; k < n; k += 32) {
       const double d = cat.dist[o0 + k];
       const double x = cat.loglam[o0 + k] - lbar;
@@ -70,8 +71,21 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(lya_catalog cat, int
       p.z = static_cast<float>(static_cast<double>(w) * static_cast<double>(dl));
       p.w = static_cast<float>(x);
       pix[pix_base + o0 + k] = p;
+      wmx = fmaxf(wmx, fabsf(p.y));
+      wdmx = fmaxf(wdmx, fabsf(p.z));
+      xmx = fmaxf(xmx, fabsf(p.w));
+      if (k + 1 < n) {
+        const float nx = static_cast<float>(cat.dist[o0 + k + 1] - dref);
+        hmn = fminf(hmn, nx - p.x);
+      }
     }
     ss = warp_sum_f64(ss);
+    for (int o = 16; o > 0; o >>= 1) {
+      wmx = fmaxf(wmx, __shfl_xor_sync(0xffffffffu, wmx, o));
+      wdmx = fmaxf(wdmx, __shfl_xor_sync(0xffffffffu, wdmx, o));
+      hmn = fminf(hmn, __shfl_xor_sync(0xffffffffu, hmn, o));
+      xmx = fmaxf(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
+    }
     if (lane == 0) {
       if (flags) atomicOr(err, flags);
       double sr, cr, sd, cd;
@@ -89,6 +103,13 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(lya_catalog cat, int
       F.ssum[gf] = (sw > 0.0) ? ss : 0.0;
       F.dref[gf] = dref_f;
       F.mock[gf] = mock;
+      F.wmax[gf] = wmx;
+      F.wdmax[gf] = wdmx;
+      // packed distances of a sorted forest may repeat after rounding; a gap
+      // of 0 (or a single pixel) is recorded as a tiny positive number, which
+      // only makes the fixed-point bound more conservative
+      F.hmin[gf] = (hmn > 1e-6f && hmn < INFINITY) ? hmn : 1e-6f;
+      F.xmax[gf] = xmx;
       if (fp) {
         auto bits = [](double v) { return static_cast<uint64_t>(__double_as_longlong(v)); };
         uint64_t x = splitmix64(static_cast<uint64_t>(gf) * 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(n));

@@ -32,139 +32,278 @@
 namespace lya {
 namespace {
 
-constexpr int kHcap = 320;       // bins per histogram array per warp (mixed)
+constexpr int kHcap = 448;       // words per chunk-histogram array per warp: bins (K+1) x (n_par+1)
+                                 // below kHcap - 32, then one dummy word per lane
+constexpr uint32_t kM15Bits = 0x4B400000u;   // bits of 1.5 * 2^23
+constexpr float kM15 = 12582912.0f;
+constexpr int kAcap = 384;       // accumulator entries per warp: rows x n_par
 constexpr int kHcap64 = 256;     // doubles per histogram array per warp (FP64)
 constexpr int kMaxSeg = 1024;    // pixel buffer cap per warp
 
-template <bool SINGLE>
-__device__ __forceinline__ void chunk_loop(const Pix* __restrict__ buf, int jlo, int jhi, float cp,
+// Knuth's TwoSum: (hi, lo) += x with the rounding error of hi + x kept in lo.
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
+// One 32-pixel chunk of forest a against pixels [jlo, jhi) of the staged
+// forest b.  Each lane keeps the current bin and its running sums in
+// registers and adds them to the shared chunk histogram only when the bin
+// changes (a run of consecutive j).  Out-of-grid pairs land in the guard
+// row / column (floor clamped with fminf); WINDOW additionally sends rows
+// outside [twin, twin + tspan] to the guard.
+// One pixel pair of a run walk (see chunk_runs).
+// Exact two-word fixed point.  v (|v| < B) is represented as
+// (hi * 2^16 + lo) * 2^-k with q = v * 2^(k-16), hi = floor(q), lo =
+// round((q - hi) * 2^16) in [0, 2^16]; sc16 = 2^(k-16) is chosen per forest
+// pair so that |q| < 2^21 for every run of in-grid pairs.  Sums of hi and of lo
+// are kept in separate 32-bit words (no carries between them), which shared
+// memory adds natively; FP32 shared-memory reductions are emulated on this
+// part and far slower.
+__device__ __forceinline__ void split_fixed(float v, float sc16, uint32_t& hi, uint32_t& lo) {
+  const float q = v * sc16;
+  const float hm = __fadd_rd(q, kM15);            // 1.5 * 2^23 + floor(q)
+  const float fr = q - (hm - kM15);               // q - floor(q), exact
+  const float lm = fmaf(fr, 65536.f, kM15);       // 1.5 * 2^23 + round(fr * 2^16)
+  hi = __float_as_uint(hm) - kM15Bits;
+  lo = __float_as_uint(lm) - kM15Bits;
+}
+
+// One pixel pair of a run walk (see chunk_runs).
+template <bool WINDOW>
+__device__ __forceinline__ void run_step(const Pix& q, float cp, float sp, float uc, float us, float wdi,
+                                         float wi, float pmax, float tmax, uint32_t stride, uint32_t base,
+                                         float scN, float scW, uint32_t guard, uint32_t twin,
+                                         uint32_t tspan, uint32_t dummy, uint32_t& cur, float& aN, float& aW) {
+  const float rp = fabsf(fmaf(-q.x, cp, uc));
+  const float rt = fmaf(q.x, sp, us);
+  const float pf = fminf(__fadd_rd(rp, kMagic), pmax);
+  const float tf = fminf(__fadd_rd(rt, kMagic), tmax);
+  uint32_t key = __float_as_uint(tf) * stride + __float_as_uint(pf);
+  if (WINDOW) key = ((__float_as_uint(tf) - kMagicBits - twin) <= tspan) ? key : guard;
+  const uint32_t chg = key != cur ? 1u : 0u;
+  // the run that ends here (if the bin changed) goes to the chunk histogram
+  uint32_t nh, nl, wh, wl;
+  split_fixed(aN, scN, nh, nl);
+  split_fixed(aW, scW, wh, wl);
+  // every lane issues its four reductions on every step (a predicated
+  // shared-memory atomic costs a branch); a lane whose run goes on adds to its
+  // own dummy word, a lane whose run ended adds the run to its bin
+  const uint32_t addr = chg ? base + (cur << 2) : dummy;
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(nh));
+  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(nl), "n"(kHcap * 4));
+  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(wh), "n"(kHcap * 8));
+  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(wl), "n"(kHcap * 12));
+  aN = chg ? 0.f : aN;
+  aW = chg ? 0.f : aW;
+  cur = key;
+  aN = fmaf(wdi, q.z, aN);
+  aW = fmaf(wi, q.y, aW);
+}
+
+// One 32-pixel chunk of forest a against pixels [jlo, jhi) of the staged
+// forest b.  Each lane keeps the current bin and its running sums in
+// registers and adds them to the shared chunk histogram only when the bin
+// changes (a run of consecutive j).  Out-of-grid pairs land in the guard
+// row / column (floor clamped with fminf); WINDOW additionally sends rows
+// outside [twin, twin + tspan] to the guard.  Pixels are read eight at a time
+// before the eight steps: the reductions write shared memory, so a later
+// load cannot be hoisted above them.
+template <bool WINDOW>
+__device__ __forceinline__ void chunk_runs(const Pix* __restrict__ buf, int jlo, int jhi, float cp,
                                            float sp, float uc, float us, float wdi, float wi,
-                                           float fnpar, float fnperp, uint32_t npar, uint32_t base,
-                                           uint32_t twin, uint32_t tspan) {
-#pragma unroll 4
-  for (int j = jlo; j < jhi; ++j) {
-    const Pix q = buf[j];
-    const float rp = fabsf(fmaf(-q.x, cp, uc));
-    const float rt = fmaf(q.x, sp, us);
-    const float pf = __fadd_rd(rp, kMagic);
-    const float tf = __fadd_rd(rt, kMagic);
-    const uint32_t idx = __float_as_uint(tf) * npar + __float_as_uint(pf);
-    const uint32_t addr = base + (idx << 2);
-    bool ok = (rp < fnpar) && (rt < fnperp);
-    if (!SINGLE) ok = ok && ((__float_as_uint(tf) - kMagicBits - twin) <= tspan);
-    if (ok) {
-      red_add_f32_shared(addr, wdi * q.z);
-      red_add_f32_shared_off<kHcap * 4>(addr, wi * q.y);
-    }
+                                           float pmax, float tmax, uint32_t stride, uint32_t base,
+                                           float scN, float scW, uint32_t guard, uint32_t twin,
+                                           uint32_t tspan, uint32_t dummy) {
+  uint32_t cur = guard;
+  float aN = 0.f, aW = 0.f;
+  int j = jlo;
+  for (; j + 8 <= jhi; j += 8) {
+    Pix q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = buf[j + u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      run_step<WINDOW>(q[u], cp, sp, uc, us, wdi, wi, pmax, tmax, stride, base, scN, scW, guard, twin, tspan,
+                       dummy, cur, aN, aW);
   }
+  for (; j < jhi; ++j)
+    run_step<WINDOW>(buf[j], cp, sp, uc, us, wdi, wi, pmax, tmax, stride, base, scN, scW, guard, twin, tspan,
+                     dummy, cur, aN, aW);
+  // the last run
+  uint32_t nh, nl, wh, wl;
+  split_fixed(aN, scN, nh, nl);
+  split_fixed(aW, scW, wh, wl);
+  const uint32_t addr = base + (cur << 2);
+  asm volatile(
+      "{\n\t"
+      "red.shared.add.u32 [%0], %1;\n\t"
+      "red.shared.add.u32 [%0+%5], %2;\n\t"
+      "red.shared.add.u32 [%0+%6], %3;\n\t"
+      "red.shared.add.u32 [%0+%7], %4;\n\t}"
+      ::"r"(addr), "r"(nh), "r"(nl), "r"(wh), "r"(wl), "n"(kHcap * 4), "n"(kHcap * 8), "n"(kHcap * 12));
 }
 
-// FP32 chunk partials -> FP64 band accumulator (and clear the partials)
-__device__ __forceinline__ void fold_chunk(float* hN, double* aN, int Lw, int lane) {
-  float* hW = hN + kHcap;
-  double* aW = aN + kHcap;
-  __syncwarp();
-  for (int k = lane; k < Lw; k += 32) {
-    const float vw = hW[k], vn = hN[k];
-    if (vw != 0.f || vn != 0.f) {
-      aW[k] += static_cast<double>(vw);
-      aN[k] += static_cast<double>(vn);
-      hW[k] = 0.f;
-      hN[k] = 0.f;
-    }
-  }
-  __syncwarp();
+// Per-pair scale sc16 = 2^(20 - e) with 2^e <= B < 2^(e+1): every |v| < B
+// maps to |q| < 2^21.
+__device__ __forceinline__ float fixed_scale(float B) {
+  if (!(B > 0.f) || !(B < 1e37f)) return 1.f;
+  const int e = static_cast<int>((__float_as_uint(B) >> 23) & 0xFFu) - 127;
+  const int ex = 20 - e + 127;
+  return __uint_as_float(static_cast<uint32_t>(min(max(ex, 1), 254)) << 23);
 }
 
-__device__ void pair_mixed(const XiArgs& A, int a, int b, float cp, float sp, float* hN, uint32_t sN,
-                           double* aN, Pix* buf, int seg, int kmax, int lane) {
-  const int na = A.F.len[a], nb = A.F.len[b];
-  if (na == 0 || nb == 0) return;
-  const Pix* __restrict__ pa = A.pix + A.F.off[a];
-  const Pix* __restrict__ pb = A.pix + A.F.off[b];
-  const float refa = A.F.dref[a], refb = A.F.dref[b];
-  const float Dc = (refa - refb) * cp;
-  const float Ds = (refa + refb) * sp;
-  const int npar = A.n_par, nperp = A.n_perp;
-  const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(nperp);
-  const float da0 = pa[0].x, daL = pa[na - 1].x, db0 = pb[0].x, dbL = pb[nb - 1].x;
-  const float rt_min = fmaf(db0, sp, fmaf(da0, sp, Ds));
-  const float rt_max = fmaf(dbL, sp, fmaf(daL, sp, Ds));
-  if (!(rt_min < fnperp)) return;
-  const int t_lo = static_cast<int>(rt_min);
-  const int t_hi = (rt_max < fnperp) ? static_cast<int>(rt_max) : nperp - 1;
-  const int64_t out_off = static_cast<int64_t>(A.F.mock[a]) * A.nb;
-  double* aW = aN + kHcap;
-  for (int tw = t_lo; tw <= t_hi; tw += kmax) {
-    const int tw_hi = min(t_hi, tw + kmax - 1);
-    const int Lw = (tw_hi - tw + 1) * npar;
-    const bool single = (tw == t_lo) && (tw_hi == t_hi);
-    const uint32_t C = kMagicBits * static_cast<uint32_t>(npar + 1) +
-                       static_cast<uint32_t>(tw) * static_cast<uint32_t>(npar);
-    const uint32_t base = sN - 4u * C;
-    for (int j0 = 0; j0 < nb; j0 += seg) {
-      const int segn = min(seg, nb - j0);
-      __syncwarp();
-      for (int k = lane; k < segn; k += 32) buf[k] = pb[j0 + k];
-      __syncwarp();
-      for (int i0 = 0; i0 < na; i0 += 32) {
-        const int i = i0 + lane;
-        // lanes past the end carry a NaN distance: every range test fails for them
-        const Pix pi = (i < na) ? pa[i] : make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, 0.f);
-        const float uc = fmaf(pi.x, cp, Dc);
-        const float us = fmaf(pi.x, sp, Ds);
-        const int last = min(31, na - 1 - i0);
-        const float uc_first = __shfl_sync(0xffffffffu, uc, 0);
-        const float us_first = __shfl_sync(0xffffffffu, us, 0);
-        const float uc_last = __shfl_sync(0xffffffffu, uc, last);
-        float dlo = (uc_first - fnpar) / cp;
-        float dhi = (uc_last + fnpar) / cp;
-        if (sp > 0.f) dhi = fminf(dhi, (fnperp - us_first) / sp);
-        dlo -= fabsf(dlo) * 1e-5f + 1e-2f;
-        dhi += fabsf(dhi) * 1e-5f + 1e-2f;
-        const int jlo = count_below(buf, segn, dlo);
-        const int jhi = count_below(buf, segn, dhi);
-        if (jlo >= jhi) continue;
-        if (single)
-          chunk_loop<true>(buf, jlo, jhi, cp, sp, uc, us, pi.z, pi.y, fnpar, fnperp, npar, base, 0, 0);
-        else
-          chunk_loop<false>(buf, jlo, jhi, cp, sp, uc, us, pi.z, pi.y, fnpar, fnperp, npar, base,
-                            static_cast<uint32_t>(tw), static_cast<uint32_t>(tw_hi - tw));
-        fold_chunk(hN, aN, Lw, lane);
+struct WarpSm {
+  uint32_t* h;      // chunk histogram: N hi, N lo, W hi, W lo (kHcap words each)
+  float* acc;       // accumulator: N hi, N lo, W hi, W lo (kAcap each)
+  Pix* buf;         // staged pixels of forest b
+  uint32_t sN;      // shared address of hN
+};
+
+// chunk rows [0, nrows) x columns [0, npar) -> accumulator rows [r0, r0+nrows)
+// (fixed point -> FP32 with the pair's scales); clears the whole chunk
+// histogram including the guard row and column
+__device__ __forceinline__ void fold_chunk(const WarpSm& w, int nrows, int npar, int r0, float inv_scN,
+                                           float inv_scW, int lane) {
+  __syncwarp();
+  const int stride = npar + 1;
+  uint32_t* nh = w.h;
+  uint32_t* nl = w.h + kHcap;
+  uint32_t* wh = w.h + 2 * kHcap;
+  uint32_t* wl = w.h + 3 * kHcap;
+  float* nhi = w.acc;
+  float* nlo = w.acc + kAcap;
+  float* whi = w.acc + 2 * kAcap;
+  float* wlo = w.acc + 3 * kAcap;
+  for (int r = 0; r <= nrows; ++r) {
+    for (int p = lane; p < stride; p += 32) {
+      const int k = r * stride + p;
+      const uint32_t a1 = nh[k], a2 = nl[k], b1 = wh[k], b2 = wl[k];
+      if ((a1 | a2 | b1 | b2) != 0u) {
+        if (r < nrows && p < npar) {
+          const int a = (r0 + r) * npar + p;
+          const float vn = fmaf(static_cast<float>(a2), 1.f / 65536.f, static_cast<float>(static_cast<int32_t>(a1))) * inv_scN;
+          const float vw = fmaf(static_cast<float>(b2), 1.f / 65536.f, static_cast<float>(static_cast<int32_t>(b1))) * inv_scW;
+          two_sum(nhi[a], nlo[a], vn);
+          two_sum(whi[a], wlo[a], vw);
+        }
+        nh[k] = 0u;
+        nl[k] = 0u;
+        wh[k] = 0u;
+        wl[k] = 0u;
       }
     }
-    __syncwarp();
-    for (int k = lane; k < Lw; k += 32) {
-      const double vw = aW[k], vn = aN[k];
-      if (vw != 0.0 || vn != 0.0) {
-        const int tt = k / npar;
-        const int p = k - tt * npar;
-        const int64_t bin = out_off + static_cast<int64_t>(p) * nperp + tw + tt;
-        red_add_f64_global(A.wsum + bin, vw);
-        red_add_f64_global(A.num + bin, vn);
-        aW[k] = 0.0;
-        aN[k] = 0.0;
-      }
-    }
-    __syncwarp();
   }
+  __syncwarp();
 }
 
-__global__ void __launch_bounds__(512) xi_mixed_kernel(XiArgs A, int seg, int kmax, int grab) {
+// accumulator rows [0, rows) with origin t0 -> FP64 bin sums in global memory
+__device__ __forceinline__ void flush_acc(const WarpSm& w, const XiArgs& A, int rows, int t0,
+                                          int64_t out_off, int lane) {
+  __syncwarp();
+  const int npar = A.n_par;
+  float* nhi = w.acc;
+  float* nlo = w.acc + kAcap;
+  float* whi = w.acc + 2 * kAcap;
+  float* wlo = w.acc + 3 * kAcap;
+  for (int r = 0; r < rows; ++r) {
+    for (int p = lane; p < npar; p += 32) {
+      const int a = r * npar + p;
+      const float h1 = nhi[a], h2 = whi[a];
+      if (h1 != 0.f || h2 != 0.f) {
+        const int64_t bin = out_off + static_cast<int64_t>(p) * A.n_perp + t0 + r;
+        red_add_f64_global(A.num + bin, static_cast<double>(h1) + static_cast<double>(nlo[a]));
+        red_add_f64_global(A.wsum + bin, static_cast<double>(h2) + static_cast<double>(wlo[a]));
+        nhi[a] = 0.f;
+        nlo[a] = 0.f;
+        whi[a] = 0.f;
+        wlo[a] = 0.f;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Bin rows t0 .. t0 + K - 1 of forest pair (a, b) into the chunk histogram
+// (origin t0) and fold them into accumulator rows r0 ..; WINDOW restricts to
+// rows [t0, t0 + K) of a wider band whose top is t_hi.
+template <bool WINDOW>
+__device__ void pair_rows(const XiArgs& A, const WarpSm& w, int aidx, int bidx, const Pix* __restrict__ pa,
+                          const Pix* __restrict__ pb, int na, int nb, float cp, float sp, float Dc,
+                          float Ds, int t0, int K, int t_hi, int r0, int seg, int lane) {
+  const int npar = A.n_par;
+  const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(A.n_perp);
+  const uint32_t stride = static_cast<uint32_t>(npar + 1);
+  // key (M+t)*(npar+1) + (M+p) -> local index (t - t0)*(npar+1) + p
+  const uint32_t C = kMagicBits * (stride + 1u) + static_cast<uint32_t>(t0) * stride;
+  const uint32_t base = w.sN - 4u * C;
+  // fixed-point scales: a run of in-grid pairs (fixed i, one bin) spans less
+  // than 2 / cp in distance, so it holds at most 2 / (cp hmin_b) + 1 pixels of b
+  const float nrun = 2.f / (cp * A.F.hmin[bidx]) + 1.f;
+  const float scN = fixed_scale(A.F.wdmax[aidx] * A.F.wdmax[bidx] * nrun);
+  const float scW = fixed_scale(A.F.wmax[aidx] * A.F.wmax[bidx] * nrun);
+  const float inv_scN = 1.f / scN, inv_scW = 1.f / scW;
+  const uint32_t guard = C + static_cast<uint32_t>(npar);   // row 0, guard column
+  const float pmax = __uint_as_float(kMagicBits + static_cast<uint32_t>(npar));
+  const float tmax = __uint_as_float(kMagicBits + static_cast<uint32_t>(t_hi + 1));
+  int pending = 0;
+  for (int j0 = 0; j0 < nb; j0 += seg) {
+    const int segn = min(seg, nb - j0);
+    __syncwarp();
+    for (int k = lane; k < segn; k += 32) w.buf[k] = pb[j0 + k];
+    __syncwarp();
+    for (int i0 = 0; i0 < na; i0 += 32) {
+      const int i = i0 + lane;
+      // lanes past the end carry a NaN distance: they only ever hit the guard
+      const Pix pi = (i < na) ? pa[i] : make_float4(__int_as_float(0x7fffffff), 0.f, 0.f, 0.f);
+      const float uc = fmaf(pi.x, cp, Dc);
+      const float us = fmaf(pi.x, sp, Ds);
+      const int last = min(31, na - 1 - i0);
+      const float uc_first = __shfl_sync(0xffffffffu, uc, 0);
+      const float us_first = __shfl_sync(0xffffffffu, us, 0);
+      const float uc_last = __shfl_sync(0xffffffffu, uc, last);
+      float dlo = (uc_first - fnpar) / cp;
+      float dhi = (uc_last + fnpar) / cp;
+      if (sp > 0.f) dhi = fminf(dhi, (fnperp - us_first) / sp);
+      dlo -= fabsf(dlo) * 1e-5f + 1e-2f;
+      dhi += fabsf(dhi) * 1e-5f + 1e-2f;
+      const int jlo = count_below(w.buf, segn, dlo);
+      const int jhi = count_below(w.buf, segn, dhi);
+      if (jlo >= jhi) continue;
+      chunk_runs<WINDOW>(w.buf, jlo, jhi, cp, sp, uc, us, pi.z, pi.y, pmax, tmax, stride, base, scN, scW,
+                         guard, static_cast<uint32_t>(t0), static_cast<uint32_t>(K - 1),
+                         w.sN + 4u * static_cast<uint32_t>(kHcap - 32 + lane));
+      if (++pending == 2) {
+        fold_chunk(w, K, npar, r0, inv_scN, inv_scW, lane);
+        pending = 0;
+      }
+    }
+  }
+  if (pending) fold_chunk(w, K, npar, r0, inv_scN, inv_scW, lane);
+}
+
+__global__ void __launch_bounds__(512, 1) xi_mixed_kernel(XiArgs A, int seg, int kmax, int grab) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per warp: FP64 band accumulator (2 x kHcap doubles), FP32 chunk
-  // histogram (2 x kHcap floats), pixel buffer (seg float4)
-  const int per_warp = kHcap * 16 + kHcap * 8 + seg * 16;
-  double* aN = reinterpret_cast<double*>(smem + wid * per_warp);
-  float* hN = reinterpret_cast<float*>(smem + wid * per_warp + kHcap * 16);
-  Pix* buf = reinterpret_cast<Pix*>(smem + wid * per_warp + kHcap * 24);
-  const uint32_t sN = smem_addr(hN);
-  for (int k = lane; k < 2 * kHcap; k += 32) {
-    hN[k] = 0.f;
-    aN[k] = 0.0;
-  }
+  // per warp: accumulator (4 x kAcap floats), chunk histogram (4 x kHcap
+  // words), pixel buffer (seg float4)
+  const int per_warp = kAcap * 16 + kHcap * 16 + seg * 16;
+  unsigned char* wb = smem + wid * per_warp;
+  WarpSm w;
+  w.acc = reinterpret_cast<float*>(wb);
+  w.h = reinterpret_cast<uint32_t*>(wb + kAcap * 16);
+  w.buf = reinterpret_cast<Pix*>(wb + kAcap * 16 + kHcap * 16);
+  w.sN = smem_addr(w.h);
+  for (int k = lane; k < 4 * kAcap; k += 32) w.acc[k] = 0.f;
+  for (int k = lane; k < 4 * kHcap; k += 32) w.h[k] = 0u;
   __syncwarp();
+  const int npar = A.n_par, nperp = A.n_perp;
+  const float fnperp = static_cast<float>(nperp);
+  // the accumulator holds rows [acc_t0, acc_t0 + kmax) of catalogue acc_off
+  int acc_t0 = -1;
+  int64_t acc_off = -1;
   for (;;) {
     unsigned long long it0 = 0;
     if (lane == 0) it0 = atomicAdd(A.counter, static_cast<unsigned long long>(grab));
@@ -174,10 +313,44 @@ __global__ void __launch_bounds__(512) xi_mixed_kernel(XiArgs A, int seg, int km
     for (int64_t it = static_cast<int64_t>(it0); it < it1; ++it) {
       const int2 ab = A.pairs[it];
       if (ab.x < 0) continue;   // rejected pair
+      const int a = ab.x, b = ab.y;
+      const int na = A.F.len[a], nb = A.F.len[b];
+      if (na == 0 || nb == 0) continue;
       const float2 cs = A.cs[it];
-      pair_mixed(A, ab.x, ab.y, cs.x, cs.y, hN, sN, aN, buf, seg, kmax, lane);
+      const float cp = cs.x, sp = cs.y;
+      const Pix* __restrict__ pa = A.pix + A.F.off[a];
+      const Pix* __restrict__ pb = A.pix + A.F.off[b];
+      const float refa = A.F.dref[a], refb = A.F.dref[b];
+      const float Dc = (refa - refb) * cp;
+      const float Ds = (refa + refb) * sp;
+      // r_perp band from the extreme pixels (r_perp is monotone in both distances)
+      const float rt_min = fmaf(pb[0].x, sp, fmaf(pa[0].x, sp, Ds));
+      const float rt_max = fmaf(pb[nb - 1].x, sp, fmaf(pa[na - 1].x, sp, Ds));
+      if (!(rt_min < fnperp)) continue;
+      const int t_lo = static_cast<int>(rt_min);
+      const int t_hi = (rt_max < fnperp) ? static_cast<int>(rt_max) : nperp - 1;
+      const int K = t_hi - t_lo + 1;
+      const int64_t out_off = static_cast<int64_t>(A.F.mock[a]) * A.nb;
+      if (K <= kmax) {
+        if (t_lo != acc_t0 || out_off != acc_off) {
+          if (acc_t0 >= 0) flush_acc(w, A, kmax, acc_t0, acc_off, lane);
+          acc_t0 = t_lo;
+          acc_off = out_off;
+        }
+        pair_rows<false>(A, w, a, b, pa, pb, na, nb, cp, sp, Dc, Ds, t_lo, K, t_hi, 0, seg, lane);
+      } else {
+        // wide band: windows of kmax rows, each flushed on its own
+        if (acc_t0 >= 0) flush_acc(w, A, kmax, acc_t0, acc_off, lane);
+        acc_t0 = -1;
+        for (int tw = t_lo; tw <= t_hi; tw += kmax) {
+          const int Kw = min(kmax, t_hi - tw + 1);
+          pair_rows<true>(A, w, a, b, pa, pb, na, nb, cp, sp, Dc, Ds, tw, Kw, t_hi, 0, seg, lane);
+          flush_acc(w, A, Kw, tw, out_off, lane);
+        }
+      }
     }
   }
+  if (acc_t0 >= 0) flush_acc(w, A, kmax, acc_t0, acc_off, lane);
 }
 
 // ----------------------------------------------------------------------------
@@ -359,14 +532,16 @@ __global__ void finalize_kernel(const double* num, const double* wsum, double* x
 
 cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps, int grab,
                           XiLaunch* L) {
-  if (n_par > kHcap) return cudaErrorInvalidValue;
+  if (2 * (n_par + 1) > kHcap - 32 || n_par > kAcap) return cudaErrorInvalidValue;
   int seg = ((std::max(max_len, 1) + 31) / 32) * 32;
   if (seg > kMaxSeg) seg = kMaxSeg;
+  // longer forests are staged in segments: shrink the segment until the block fits
+  while (seg > 32 && warps * (kAcap * 16 + kHcap * 16 + seg * 16) > dev.smem_optin) seg -= 32;
   L->warps = warps;
   L->hcap = kHcap;
   L->seg = seg;
   L->grab = grab;
-  L->smem = warps * (kHcap * 24 + seg * 16);
+  L->smem = warps * (kAcap * 16 + kHcap * 16 + seg * 16);
   if (L->smem > dev.smem_optin) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(xi_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        L->smem);
@@ -383,7 +558,9 @@ cudaError_t launch_xi_mixed(const XiArgs& a, const XiLaunch& L, cudaStream_t s) 
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (a.n_pairs == 0) return cudaSuccess;
-  const int kmax = std::max(1, std::min(a.n_perp, kHcap / a.n_par));
+  // band rows per window: the chunk histogram needs (kmax + 1) x (n_par + 1)
+  // entries (guard row and column), the accumulator kmax x n_par
+  const int kmax = std::max(1, std::min({a.n_perp, (kHcap - 32) / (a.n_par + 1) - 1, kAcap / a.n_par}));
   LYA_COUNT(1), xi_mixed_kernel<<<L.blocks, L.warps * 32, L.smem, s>>>(a, L.seg, kmax, L.grab);
   return cudaGetLastError();
 }
