@@ -36,6 +36,17 @@ x = Lambda - Lbar) multiplied out.  With, for one forest pair,
 where each term whose forest term of eta is dropped (W = 0 or S = 0, see
 ``oracle.project``) is absent.  W_a and S_a run over all pixels of forest a.
 The tests check the two forms against each other.
+
+Edge allowance (``eps_edge`` > 0).  A pixel pair (k, l) whose scaled
+separation lies within eps of a bin edge may be binned in any of its candidate
+bins (the same candidates as ``oracle.xi``) by a separation computed with an
+error below eps.  Moving it changes column B of D~ by
+v_kl[A] = sum_{(i,j) in A} w_i w_j eta_ik eta_jl in every row A, and, since
+w_i eta_ik = w_k eta_ki, row B by the transpose.  ``edge_d[A, B]`` bounds
+|change of D~_AB| for any such rebinning of the ambiguous pairs: the sum of
+|v_kl[A]| over ambiguous (k, l) with candidate B, the same transposed, and
+|w_i w_j eta_ik eta_jl| for every two ambiguous pairs (i, j), (k, l) of a
+forest pair whose candidates include A and B (both moved).
 """
 from __future__ import annotations
 
@@ -75,11 +86,51 @@ def dmat_literal(cat, bins, pair_list=None, eta_identity: bool = False):
     return {"dmat": D, "dtilde": dt, "wsum": wdm}
 
 
+def _edge_terms(A, x, y, ii, jj, wa, wb, ea, eb, eps, bins, E, E2):
+    """Edge allowance of one forest pair (see the module docstring).
+
+    For every pixel pair (k, l) within eps of a bin edge, |v_kl| is added to
+    column B of E for each candidate bin B; for every two such pairs (i, j),
+    (k, l) (the same pair included), |w_i w_j eta_ik eta_jl| is added to E2 at
+    every (candidate of (i, j), candidate of (k, l)).  Index nb is a dummy
+    row / column for the unused candidate slots."""
+    nb = bins.nbins
+    p_lo = np.floor(np.maximum(x - eps, 0.0))
+    p_hi = np.floor(x + eps)
+    t_lo = np.floor(np.maximum(y - eps, 0.0))
+    t_hi = np.floor(y + eps)
+    amb = (p_lo != p_hi) | (t_lo != t_hi)
+    ka, la = np.nonzero(amb)
+    if len(ka) == 0:
+        return
+    cands = np.full((len(ka), 4), nb, dtype=np.int64)
+    for s_, (pp, tt) in enumerate(((p_lo, t_lo), (p_hi, t_lo), (p_lo, t_hi), (p_hi, t_hi))):
+        pv, tv = pp[ka, la], tt[ka, la]
+        inside = (pv < bins.n_par) & (tv < bins.n_perp)
+        cands[:, s_] = np.where(inside, (pv * bins.n_perp + tv).astype(np.int64), nb)
+    # the same bin may appear in several slots: keep the first
+    for s_ in range(1, 4):
+        dup = np.any(cands[:, :s_] == cands[:, s_:s_ + 1], axis=1)
+        cands[dup, s_] = nb
+    rows = A[ii, jj]
+    for q, (k, l) in enumerate(zip(ka, la)):
+        v = np.abs(np.bincount(rows, weights=(wa[ii] * ea[ii, k]) * (wb[jj] * eb[jj, l]), minlength=nb + 1))
+        for B in cands[q]:
+            E[:, B] += v
+    T = np.abs((wa[ka][:, None] * ea[np.ix_(ka, ka)]) * (wb[la][:, None] * eb[np.ix_(la, la)]))
+    for s1 in range(4):
+        for s2 in range(4):
+            np.add.at(E2, (cands[:, s1][:, None], cands[:, s2][None, :]), T)
+
+
 def _dm_chunk(cat, bins, a_arr, b_arr, extra):
     eta_identity = extra["eta_identity"]
+    eps = extra.get("eps_edge", 0.0)
     nb = bins.nbins
     dt = np.zeros((nb, nb))
     wdm = np.zeros(nb)
+    E = np.zeros((nb + 1, nb + 1)) if eps > 0.0 else None
+    E2 = np.zeros((nb + 1, nb + 1)) if eps > 0.0 else None
     nvec = unit_vectors(cat.ra, cat.dec)
     for a, b in zip(a_arr, b_arr):
         sa, sb = cat.forest(a), cat.forest(b)
@@ -87,10 +138,18 @@ def _dm_chunk(cat, bins, a_arr, b_arr, extra):
         if na == 0 or nbp == 0:
             continue
         c, s = half_angle(nvec[a], nvec[b])
-        A, ok, _, _ = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
+        A, ok, x, y = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
         if not np.any(ok):
             continue
         ii, jj = np.nonzero(ok)
+        if E is not None:
+            w_a = cat.weight[sa].astype(np.float64)
+            w_b = cat.weight[sb].astype(np.float64)
+            if eta_identity:
+                ea, eb = np.eye(na), np.eye(nbp)
+            else:
+                ea, eb = eta_matrix(w_a, cat.loglam[sa]), eta_matrix(w_b, cat.loglam[sb])
+            _edge_terms(A, x, y, ii, jj, w_a, w_b, ea, eb, eps, bins, E, E2)
         uniq, loc = np.unique(A[ii, jj], return_inverse=True)
         L = len(uniq)
         wa = cat.weight[sa].astype(np.float64)
@@ -128,15 +187,22 @@ def _dm_chunk(cat, bins, a_arr, b_arr, extra):
                 D += np.outer(Txy, Txy) / (Sa * Sb)
         dt[np.ix_(uniq, uniq)] += D
         wdm[uniq] += T1
-    return {"dtilde": dt, "wsum": wdm}
+    out = {"dtilde": dt, "wsum": wdm}
+    if E is not None:
+        E, E2 = E[:nb, :nb], E2[:nb, :nb]
+        out["edge_d"] = E + E.T + E2
+    return out
 
 
-def dmat(cat, bins, pair_list=None, eta_identity: bool = False, processes: int = 1):
-    """Eq. (2.6) via the expanded eta.  Returns dict(dmat, dtilde, wsum)."""
+def dmat(cat, bins, pair_list=None, eta_identity: bool = False, processes: int = 1,
+         eps_edge: float = 0.0):
+    """Eq. (2.6) via the expanded eta.  Returns dict(dmat, dtilde, wsum) and,
+    with eps_edge > 0, the column edge allowance edge_d (module docstring)."""
     if pair_list is None:
         pair_list = _pairs.forest_pairs(cat, bins)
     a, b = pair_list
-    out = map_pairs(_dm_chunk, cat, bins, a, b, {"eta_identity": bool(eta_identity)},
+    out = map_pairs(_dm_chunk, cat, bins, a, b,
+                    {"eta_identity": bool(eta_identity), "eps_edge": float(eps_edge)},
                     processes=processes, chunk=200)
     w = out["wsum"]
     out["dmat"] = np.divide(out["dtilde"], w[:, None], out=np.zeros_like(out["dtilde"]),

@@ -163,3 +163,25 @@ def test_two_pixel_forests_are_annihilated():
     out = odm.dmat(cat, synth.Bins(6, 2, 24.0, 8.0), pairs.all_pairs(4))
     assert np.max(np.abs(out["dtilde"])) < 1e-12
     assert out["wsum"].sum() > 0
+
+
+def test_dmat_edge_allowance_brackets_shifted_binning(cat0, bins0):
+    """Moving every scaled separation by less than eps changes each D~_AB by
+    at most edge_d[A, B]; the bound is not vacuous (pairs do move)."""
+    sub = synth.subset(cat0, np.arange(25))
+    eps = 1e-3
+    pr = pairs.forest_pairs(sub, bins0)
+    base = odm.dmat(sub, bins0, pr, eps_edge=eps)
+    E = base["edge_d"]
+    np.testing.assert_allclose(E, E.T, rtol=1e-12)
+    moved_any = False
+    for scale in [1 + 0.9 * eps / 25, 1 - 0.9 * eps / 25]:
+        b2 = synth.Bins(bins0.n_par, bins0.n_perp, bins0.r_par_max / scale, bins0.r_perp_max / scale)
+        moved = odm.dmat(sub, b2, pr)
+        diff = np.abs(moved["dtilde"] - base["dtilde"])
+        moved_any |= bool(np.any(diff > 1e-6 * np.abs(base["dtilde"]).max()))
+        assert np.all(diff <= E * (1 + 1e-9) + 1e-9 * np.abs(base["dtilde"]).max())
+    assert moved_any
+    # the allowance is small where nothing is near an edge: zero without ambiguous pairs
+    far = odm.dmat(sub, bins0, pr, eps_edge=1e-12)
+    assert far["edge_d"].sum() < 1e-6 * E.sum()
