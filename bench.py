@@ -30,6 +30,8 @@ import numpy as np  # noqa: E402
 
 WORKLOAD = {"workload": "sdss_dr16_like_60k", "forests": 60000, "area_deg2": 2500,
             "bins": "50x50 of 4 Mpc/h", "dm_subsample": 0.05, "grid": "log10 step 3e-4"}
+WORKLOAD_DESI = {"workload": "desi_y5_like_600k", "forests": 600000, "area_deg2": 10000,
+                 "bins": "50x50 of 4 Mpc/h", "grid": "linear 0.8 A, 100-600 px, continuum tilt projected out"}
 METRIC = "pixel pairs/s (xi+W) and DM pair-pairs/s at 1 GB300; fraction of FP32 roofline"
 DM_P, DM_SEED = 0.05, 1234
 FLOPS_PER_PAIR = 8  # 4 for the two scaled separations, 2 products, 2 accumulations
@@ -316,6 +318,7 @@ def run_ours(args, rank, world, local):
     peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
     dominant = max(med, key=med.get)
+    graph = None if args.no_graph else graph_replay(api, synth, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(cat, bins, 6e9)
@@ -339,12 +342,183 @@ def run_ours(args, rank, world, local):
                "pair_pairs": dm["pixel_pairs_sq"], "forest_pairs": dm["forest_pairs"],
                "pixel_pairs": dm["pixel_pairs"]},
         "fp64_path": fp64,
+        "graph_replay": graph,
         "autotune_choice": tune,
         "e2e": {"value": pix_total / e2e_s, "unit": "pixel pairs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
+def graph_replay(api, synth, dev, iters: int = 20):
+    """Eager calls vs a captured CUDA graph for the tiny workload (200 forests,
+    25 x 25 bins): project + xi/W + adjoint + D, per iteration, on one stream."""
+    import torch
+    cat = synth.make(0)
+    bins = synth.bins_for(0)
+    nb = bins.nbins
+    dc = api.DeviceCatalog.from_host(cat, device=dev)
+    h = api.Handle()
+    o = {"dp": torch.empty_like(dc.delta), "num": torch.empty(nb, dtype=torch.float64, device=dev),
+         "wsum": torch.empty(nb, dtype=torch.float64, device=dev), "xi": torch.empty(nb, dtype=torch.float64, device=dev),
+         "gd": torch.empty_like(dc.delta), "gw": torch.empty_like(dc.weight),
+         "D": torch.empty((nb, nb), dtype=torch.float64, device=dev), "Wd": torch.empty(nb, dtype=torch.float64, device=dev)}
+    g = torch.from_numpy(np.random.default_rng(303).normal(size=nb)).to(dev)
+    s = torch.cuda.Stream(device=dev)
+
+    def calls():
+        dcp = dc.with_(delta=o["dp"])
+        api.lya_project(h, dc, out=o["dp"], stream=s)
+        api.lya_xi(h, dcp, bins, "mixed", o["num"], o["wsum"], o["xi"], stream=s)
+        api.lya_xi_backward(h, dcp, bins, g, o["xi"], o["wsum"], stream=s, grad_delta=o["gd"], grad_weight=o["gw"])
+        api.lya_dmat(h, dcp, bins, 1.0, 3, stream=s, D=o["D"], W=o["Wd"])
+
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            calls()
+        api.lya_sync_status(h, s)
+        api.lya_capture_begin(h, s)
+        calls()
+        gr = api.lya_capture_end(h)
+        for _ in range(3):
+            gr.launch(s)
+        s.synchronize()
+        k0 = api.lya_kernel_launches()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            calls()
+        s.synchronize()
+        eager_ms = (time.perf_counter() - t0) * 1e3 / iters
+        k1 = api.lya_kernel_launches()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            gr.launch(s)
+        s.synchronize()
+        graph_ms = (time.perf_counter() - t0) * 1e3 / iters
+        k2 = api.lya_kernel_launches()
+    gr.close()
+    h.close()
+    return {"workload": "tiny_200_forests", "step": "project + xi/W + adjoint + D (p = 1)",
+            "eager_ms_per_iter": eager_ms, "graph_ms_per_iter": graph_ms,
+            "kernels_per_iter": (k1 - k0) / iters, "graph_kernels_per_iter": (k2 - k1) / iters,
+            "iters": iters}
+
+
+def run_desi(args, rank, world, local):
+    """The DESI-Y5-like catalogue (600,000 forests): project + pair list +
+    xi/W (mixed) per step, and the plain-FP64 path beside the mixed one on a
+    seeded 0.5% sample of the forest pairs."""
+    import torch
+    from paper_2507_00129_gb300 import synth, build
+    build.build()
+    from paper_2507_00129_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = synth.spec_for(2, seed=2 + rank)
+    if args.forests:
+        spec.area_deg2 = spec.area_deg2 * args.forests / spec.n_forests
+        spec.n_forests = args.forests
+    t_gen = time.perf_counter()
+    cat = synth.generate(spec, name="desi_like")
+    t_gen = time.perf_counter() - t_gen
+    bins = synth.bins_for(2)
+    nb = bins.nbins
+    dc = api.DeviceCatalog.from_host(cat, device=dev)
+    del cat
+    h = api.Handle()
+    dp = torch.empty_like(dc.delta)
+    dcp = dc.with_(delta=dp)
+    num = torch.empty(nb, dtype=torch.float64, device=dev)
+    wsum = torch.empty_like(num)
+    xi = torch.empty_like(num)
+    # launch shape tuned on a 30,000-forest catalogue of the same kind (same bins)
+    tspec = synth.spec_for(2, seed=1000 + rank, n_forests=30000)
+    tspec.area_deg2 = spec.area_deg2 * 30000 / spec.n_forests
+    tcat = api.DeviceCatalog.from_host(synth.generate(tspec), device=dev)
+    tune = api.lya_autotune(h, tcat, bins)
+    del tcat
+    api.lya_project(h, dc, out=dp)
+    st = api.lya_pair_stats(h, dcp, bins, 1.0)
+
+    def step():
+        api.lya_project(h, dc, out=dp)
+        api.lya_pairs_build(h, dcp, bins)
+        api.lya_xi(h, dcp, bins, "mixed", num, wsum, xi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    stage = {"xi": [], "pairs": []}
+    launches0 = api.lya_kernel_launches()
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+            for k in stage:
+                stage[k].append(api.lya_stage_ms(h, k))
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = api.lya_kernel_launches() - launches0
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms, pix_total, value = aggregate(ms_local, float(st["pixel_pairs"]), world)
+    med = {k: float(np.median(v)) for k, v in stage.items()}
+
+    # plain FP64 beside mixed on a seeded 0.5% sample of the forest pairs
+    n = api.lya_pairs_build(h, dcp, bins)
+    pa, pb = api.lya_pairs_get(h, n)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    sel = torch.rand(n, generator=gen, device=dev) < 0.005
+    sa, sb = pa[sel].contiguous(), pb[sel].contiguous()
+    del pa, pb, sel
+    sub = {}
+    for prec in ("mixed", "fp64"):
+        api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
+        torch.cuda.synchronize()
+        api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
+        sub[prec] = api.lya_stage_ms(h, "xi")
+    # in-grid pixel pairs of the sample (counted with the mixed binning)
+    _, wcount, _ = api.lya_xi_pairs(h, dcp.with_(weight=torch.ones_like(dc.weight)), bins, sa, sb, "mixed")
+    sample_pix = float(wcount.sum())
+
+    pk, how = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD_DESI, **({"forests": args.forests} if args.forests else {}),
+                       l2="inputs larger than L2 (catalogue 4.8 GB; packed pixels 3.2 GB)",
+                       step="project + pair list + xi/W mixed", seeds=f"catalogue seed 2+rank"),
+        "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
+                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": None,
+                     "peak_note": f"FP32 FMA peak {n_sm} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz "
+                                  f"(sm_max of {how} peaks); {FLOPS_PER_PAIR} algorithmic flops per "
+                                  "in-grid pixel pair"},
+        "stages_ms": med,
+        "xi_kernel": {"pixel_pairs_per_s": st["pixel_pairs"] / (med["xi"] / 1e3),
+                      "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"]},
+        "fp64_vs_mixed_on_sample": {"forest_pairs": int(sa.numel()), "pixel_pairs": sample_pix,
+                                    "mixed_ms": sub["mixed"], "fp64_ms": sub["fp64"],
+                                    "mixed_pixel_pairs_per_s": sample_pix / (sub["mixed"] / 1e3),
+                                    "fp64_pixel_pairs_per_s": sample_pix / (sub["fp64"] / 1e3)},
+        "autotune_choice": tune, "generate_s": t_gen,
+        "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": None, "e2e": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -360,11 +534,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--forests", type=int, default=0,
-                    help="profiling: use this many forests (same sky density) instead of 60,000")
+                    help="profiling: use this many forests (same sky density) instead of the workload's")
+    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi"],
+                    help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi")
+    ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "desi":
+        run_desi(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -238,8 +238,47 @@ int lya_xi_pairs_static(const lya_catalog* cat, const lya_bins* bins, const int3
                         void* stream);
 
 /* Number of CUDA kernels this library has launched in the calling process
- * since it was loaded (all handles).  Host-only; never fails. */
+ * since it was loaded (all handles).  Host-only; never fails.  A graph replay
+ * (lya_graph_launch) counts the kernels it holds. */
 int64_t lya_kernel_launches(void);
+
+/* ---- CUDA-graph capture of a sequence of calls --------------------------
+ * Repeated evaluations on one catalogue geometry with new deltas or weights
+ * (field-level inference, many noise realisations of one mock footprint)
+ * can replay a captured launch sequence instead of paying per-call launch and
+ * host-synchronisation costs.  This batching of launches has no counterpart in
+ * the paper, which launches one kernel per forest from Python (Section 3.1).
+ *
+ * lya_capture_begin starts a stream capture (thread-local mode) on `stream`,
+ * which must not be the legacy default stream (NULL).  Until lya_capture_end,
+ * calls of lya_project, lya_xi (MIXED only), lya_xi_batched (MIXED only),
+ * lya_dmat and lya_xi_backward on this handle and this stream are recorded,
+ * not run.  While capturing they:
+ *  - need the pair list of the same inputs cached (run each call once before
+ *    capturing) and skip the geometry check, so ra, dec, dist and offsets
+ *    must keep their values between replays; delta and weight are re-read by
+ *    every replay (their pointers are fixed at capture);
+ *  - allocate nothing: a buffer that would have to grow fails the call with
+ *    LYA_ERR_INVALID_ARG (again: run the same calls once before capturing);
+ *  - fail with LYA_ERR_INVALID_ARG if they would synchronise (lya_sync_status,
+ *    lya_pairs_build, lya_pairs_get, lya_xi_pairs, lya_autotune,
+ *    lya_pair_stats, lya_stage_ms, lya_last_launch) or use another stream.
+ * Input checks still run on the device at every replay; read them with
+ * lya_sync_status after a replay.  Outputs (caller pointers and the handle's
+ * scratch) are fixed at capture.
+ *
+ * lya_capture_end ends the capture and instantiates it; *out receives the
+ * graph (NULL on failure).  It fails if any call inside the capture failed.
+ * lya_graph_launch replays it on any stream (asynchronous).  It refuses to run
+ * (LYA_ERR_INVALID_ARG) if the handle has been destroyed, is capturing, or has
+ * reallocated one of its buffers since the capture (a call on larger inputs,
+ * or a different bin grid), because the graph would use freed memory.
+ * lya_graph_destroy releases the graph (not the handle). */
+typedef struct lya_graph lya_graph;
+int lya_capture_begin(lya_handle* h, void* stream);
+int lya_capture_end(lya_handle* h, lya_graph** out);
+int lya_graph_launch(lya_graph* g, void* stream);
+int lya_graph_destroy(lya_graph* g);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,10 @@ SIGNATURES = {
     "lya_xi_pairs_static": (c_int, [CAT, BINS, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
                                     c_void_p]),
     "lya_kernel_launches": (c_int64, []),
+    "lya_capture_begin": (c_int, [H, c_void_p]),
+    "lya_capture_end": (c_int, [H, POINTER(c_void_p)]),
+    "lya_graph_launch": (c_int, [c_void_p, c_void_p]),
+    "lya_graph_destroy": (c_int, [c_void_p]),
 }
 
 _LIB = None

@@ -186,10 +186,10 @@ def lya_xi_pairs_static(cat: DeviceCatalog, bins, pair_a: torch.Tensor, pair_b: 
 
 
 def lya_dmat(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed: int,
-             eta: str = "mean_slope", stream=None):
+             eta: str = "mean_slope", stream=None, D=None, W=None):
     nb = bins.n_par * bins.n_perp
-    D = torch.empty((nb, nb), dtype=torch.float64, device="cuda")
-    W = torch.empty(nb, dtype=torch.float64, device="cuda")
+    D = torch.empty((nb, nb), dtype=torch.float64, device="cuda") if D is None else D
+    W = torch.empty(nb, dtype=torch.float64, device="cuda") if W is None else W
     e = _lib.LYA_ETA_MEAN_SLOPE if eta == "mean_slope" else _lib.LYA_ETA_IDENTITY
     c, b = cat.c(), c_bins(bins)
     check(handle.h, _lib.load().lya_dmat(handle.h, ctypes.byref(c), ctypes.byref(b), e, float(p_subsample),
@@ -198,9 +198,9 @@ def lya_dmat(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed:
 
 
 def lya_xi_backward(handle: Handle, cat: DeviceCatalog, bins, grad_xi: torch.Tensor, xi: torch.Tensor,
-                    wsum: torch.Tensor, stream=None):
-    gd = torch.empty_like(cat.delta)
-    gw = torch.empty_like(cat.weight)
+                    wsum: torch.Tensor, stream=None, grad_delta=None, grad_weight=None):
+    gd = torch.empty_like(cat.delta) if grad_delta is None else grad_delta
+    gw = torch.empty_like(cat.weight) if grad_weight is None else grad_weight
     g = grad_xi.to(torch.float64).contiguous()
     c, b = cat.c(), c_bins(bins)
     check(handle.h, _lib.load().lya_xi_backward(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(g),
@@ -259,6 +259,41 @@ def lya_stage_ms(handle: Handle, stage: str) -> float:
 
 def lya_kernel_launches() -> int:
     return int(_lib.load().lya_kernel_launches())
+
+
+class Graph:
+    """A captured launch sequence (``lya_graph``); ``launch`` replays it.
+    Keeps its handle alive (the graph reads and writes the handle's buffers)."""
+
+    def __init__(self, ptr, handle: Handle):
+        self._g = ptr
+        self._handle = handle
+
+    def launch(self, stream=None):
+        check(self._handle.h, _lib.load().lya_graph_launch(self._g, _stream(stream)))
+
+    def close(self):
+        if self._g:
+            _lib.load().lya_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lya_capture_begin(handle: Handle, stream):
+    """Start recording the calls made on ``handle`` with ``stream`` (a
+    non-default torch.cuda.Stream).  Every output must be preallocated."""
+    check(handle.h, _lib.load().lya_capture_begin(handle.h, _stream(stream)))
+
+
+def lya_capture_end(handle: Handle) -> Graph:
+    g = ctypes.c_void_p()
+    check(handle.h, _lib.load().lya_capture_end(handle.h, ctypes.byref(g)))
+    return Graph(g, handle)
 
 
 # ---------------------------------------------------------------------------

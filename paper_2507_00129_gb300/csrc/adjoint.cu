@@ -10,8 +10,9 @@
 // atomics, deterministic.  Each pixel pair is binned with the same FP32
 // operations, in the same operand roles, as the forward kernel (first forest
 // of the stored pair on the "i" side), so forward and backward agree on every
-// bin.  Per-neighbour FP32 partial sums are added into two-term (hi, lo)
-// accumulators (Knuth's TwoSum).
+// bin.  The table has a zero guard row and column; out-of-grid pairs are
+// clamped into them, so the inner loop has no branch.  Per-neighbour FP32
+// partial sums are added into two-term (hi, lo) accumulators (Knuth's TwoSum).
 #include <algorithm>
 
 #include "lya_internal.cuh"
@@ -113,21 +114,33 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(AdjArgs A, cons
                                                                  const int64_t* n_items_dev, int seg,
                                                                  unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const int nbins = A.n_par * A.n_perp;
+  const int npar = A.n_par, nperp = A.n_perp;
+  // table entry (p, t) at p * (n_perp + 1) + t; row p = n_par and column
+  // t = n_perp are the zero guard
+  const int tstride = nperp + 1;
+  const int tab_n = (npar + 1) * tstride;
   float2* table = reinterpret_cast<float2*>(sm);
-  const int tab_bytes = ((nbins * 8) + 15) & ~15;
+  const int tab_bytes = ((tab_n * 8) + 15) & ~15;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float4* buf = reinterpret_cast<float4*>(sm + tab_bytes + wid * seg * 16);
-  for (int k = threadIdx.x; k < nbins; k += blockDim.x) {
-    const double w = A.wsum[k];
-    const double g = (w != 0.0) ? A.grad_xi[k] / w : 0.0;
-    table[k] = make_float2(static_cast<float>(g), static_cast<float>(g * A.xi[k]));
+  for (int k = threadIdx.x; k < tab_n; k += blockDim.x) {
+    const int p = k / tstride, t = k - p * tstride;
+    float2 e = make_float2(0.f, 0.f);
+    if (p < npar && t < nperp) {
+      const int bin = p * nperp + t;
+      const double w = A.wsum[bin];
+      const double g = (w != 0.0) ? A.grad_xi[bin] / w : 0.0;
+      e = make_float2(static_cast<float>(g), static_cast<float>(g * A.xi[bin]));
+    }
+    table[k] = e;
   }
   __syncthreads();
+  // key (M + p) * tstride + (M + t), M = bits of 2^23, minus this offset is p * tstride + t
   const uint32_t tbase = smem_addr(table) -
-                         8u * (kMagicBits * static_cast<uint32_t>(A.n_perp) + kMagicBits);
-  const int npar = A.n_par, nperp = A.n_perp;
+                         8u * (kMagicBits * static_cast<uint32_t>(tstride) + kMagicBits);
   const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(nperp);
+  const float pmax = __uint_as_float(kMagicBits + static_cast<uint32_t>(npar));
+  const float tmax = __uint_as_float(kMagicBits + static_cast<uint32_t>(nperp));
   const int64_t n_items = *n_items_dev;
   for (;;) {
     unsigned long long it = 0;
@@ -187,14 +200,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(AdjArgs A, cons
             const float4 q = buf[j];
             const float rp = fabsf(fmaf(-q.x, cp, uc));
             const float rt = fmaf(q.x, sp, us);
-            const float pf = __fadd_rd(rp, kMagic), tf = __fadd_rd(rt, kMagic);
-            if (valid && rp < fnpar && rt < fnperp) {
-              const uint32_t idx = __float_as_uint(pf) * static_cast<uint32_t>(nperp) + __float_as_uint(tf);
-              float2 gr;
-              asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(gr.x), "=f"(gr.y) : "r"(tbase + (idx << 3)));
-              a1 = fmaf(gr.x, q.z, a1);
-              a2 = fmaf(gr.y, q.y, a2);
-            }
+            const float pf = fminf(__fadd_rd(rp, kMagic), pmax), tf = fminf(__fadd_rd(rt, kMagic), tmax);
+            const uint32_t idx = __float_as_uint(pf) * static_cast<uint32_t>(tstride) + __float_as_uint(tf);
+            float2 gr;
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(gr.x), "=f"(gr.y) : "r"(tbase + (idx << 3)));
+            a1 = fmaf(gr.x, q.z, a1);
+            a2 = fmaf(gr.y, q.y, a2);
           }
         } else {
           // lanes are second-forest pixels; loop over first-forest pixels
@@ -217,14 +228,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(AdjArgs A, cons
             const float4 q = buf[j];
             const float rp = fabsf(fmaf(-dme, cp, q.x));
             const float rt = fmaf(dme, sp, q.y);
-            const float pf = __fadd_rd(rp, kMagic), tf = __fadd_rd(rt, kMagic);
-            if (valid && rp < fnpar && rt < fnperp) {
-              const uint32_t idx = __float_as_uint(pf) * static_cast<uint32_t>(nperp) + __float_as_uint(tf);
-              float2 gr;
-              asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(gr.x), "=f"(gr.y) : "r"(tbase + (idx << 3)));
-              a1 = fmaf(gr.x, q.w, a1);
-              a2 = fmaf(gr.y, q.z, a2);
-            }
+            const float pf = fminf(__fadd_rd(rp, kMagic), pmax), tf = fminf(__fadd_rd(rt, kMagic), tmax);
+            const uint32_t idx = __float_as_uint(pf) * static_cast<uint32_t>(tstride) + __float_as_uint(tf);
+            float2 gr;
+            asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(gr.x), "=f"(gr.y) : "r"(tbase + (idx << 3)));
+            a1 = fmaf(gr.x, q.w, a1);
+            a2 = fmaf(gr.y, q.z, a2);
           }
         }
       }
@@ -291,12 +300,12 @@ cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, si
   LYA_COUNT(1), scan1_kernel<<<1, 1024, 0, s>>>(nch, nf, coff);
   LYA_COUNT(1), item_fill_kernel<<<grid_for(nf, 256), 256, 0, s>>>(a.F, coff, items);
   LYA_TRY(cudaGetLastError());
-  const int nbins = a.n_par * a.n_perp;
+  const int tab_n = (a.n_par + 1) * (a.n_perp + 1);
   int seg = ((std::max(a.max_len, 1) + 31) / 32) * 32;
   if (seg > 1024) seg = 1024;
-  const int smem = ((nbins * 8 + 15) & ~15) + kAdjWarps * seg * 16;
+  const int smem = ((tab_n * 8 + 15) & ~15) + kAdjWarps * seg * 16;
   if (smem > dev.smem_optin) return cudaErrorInvalidValue;
-  LYA_TRY(cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(adjoint_kernel), smem));
   int per_sm = 0;
   LYA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adjoint_kernel, kAdjWarps * 32, smem));
   if (per_sm < 1) return cudaErrorInvalidValue;

@@ -11,14 +11,41 @@
 #include "lya_internal.cuh"
 
 #include <atomic>
+#include <memory>
+#include <mutex>
 
 namespace lya {
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static thread_local bool t_capturing = false;
+bool capturing_thread() { return t_capturing; }
+
+cudaError_t set_max_dynamic_smem(const void* func, int bytes) {
+  // (device, function) -> largest value set; a handful of kernels, one device in practice
+  struct Entry { int dev; const void* f; int bytes; };
+  static Entry tab[64];
+  static int n = 0;
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int k = 0; k < n; ++k)
+    if (tab[k].dev == dev && tab[k].f == func && tab[k].bytes >= bytes) return cudaSuccess;
+  if (t_capturing) return cudaErrorNotPermitted;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < n; ++k)
+    if (tab[k].dev == dev && tab[k].f == func) { tab[k].bytes = bytes; return cudaSuccess; }
+  if (n < 64) tab[n++] = Entry{dev, func, bytes};
+  return cudaSuccess;
+}
+
 cudaError_t grow(void** p, size_t* cap, size_t need) {
   if (need <= *cap && *p) return cudaSuccess;
+  if (t_capturing) return cudaErrorNotPermitted;
   if (*p) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return e;
@@ -121,19 +148,64 @@ struct lya_handle {
   // stage timing events: [stage][begin, end]
   cudaEvent_t ev[4][2] = {};
   bool ev_used[4] = {false, false, false, false};
+  // graph capture (lya_capture_begin .. lya_capture_end)
+  bool capturing = false;
+  bool cap_failed = false;
+  cudaStream_t cap_stream = nullptr;
+  long long cap_launches0 = 0;
+  std::shared_ptr<bool> alive = std::make_shared<bool>(true);
+};
+
+// A captured launch sequence and the handle buffers it reads and writes.
+struct lya_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  lya_handle* h = nullptr;
+  std::shared_ptr<bool> alive;
+  std::vector<const void*> bufs;
+  long long kernels = 0;
 };
 
 namespace {
 
-void stage_begin(lya_handle* h, int k, cudaStream_t s) { cudaEventRecord(h->ev[k][0], s); }
+void stage_begin(lya_handle* h, int k, cudaStream_t s) {
+  if (!h->capturing) cudaEventRecord(h->ev[k][0], s);
+}
 void stage_end(lya_handle* h, int k, cudaStream_t s) {
+  if (h->capturing) return;
   cudaEventRecord(h->ev[k][1], s);
   h->ev_used[k] = true;
 }
 
 int fail(lya_handle* h, int code, const std::string& msg) {
-  if (h) h->err = msg;
+  if (h) {
+    h->err = msg;
+    if (h->capturing) h->cap_failed = true;
+  }
   return code;
+}
+
+// Entry points that synchronise, read back or may rebuild the pair list are
+// refused while the handle captures a graph; the others must use the
+// capturing stream.
+int refuse_in_capture(lya_handle* h, const char* what) {
+  if (!h->capturing) return LYA_OK;
+  return fail(h, LYA_ERR_INVALID_ARG, std::string(what) + " synchronises: not allowed during graph capture");
+}
+int check_capture_stream(lya_handle* h, cudaStream_t s) {
+  if (h->capturing && s != h->cap_stream)
+    return fail(h, LYA_ERR_INVALID_ARG, "during graph capture every call must use the capturing stream");
+  return LYA_OK;
+}
+
+std::vector<const void*> handle_buffers(const lya_handle* h) {
+  return {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->F_capacity)),
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->pix_cap)),
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->scratch_cap)),
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->scratch2_cap)),
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->out_cap)),
+          reinterpret_cast<const void*>(static_cast<uintptr_t>(h->g_cap))};
 }
 
 int cuda_fail(lya_handle* h, cudaError_t e, const char* where) {
@@ -191,6 +263,8 @@ int read_flags(lya_handle* h, cudaStream_t s, unsigned* out) {
 // Forest and pixel workspace for n forests / p pixels.  Reallocates (losing
 // the cached pair list) only when capacity is short.
 int ensure_workspace(lya_handle* h, int64_t nf, int64_t np) {
+  if (h->capturing && (nf > h->F_capacity || !h->fbuf))
+    return fail(h, LYA_ERR_INVALID_ARG, "graph capture: forest workspace too small (run the call once before capturing)");
   if (nf > h->F_capacity || !h->fbuf) {
     const int64_t cap = std::max<int64_t>(nf, 1) + std::max<int64_t>(nf, 1) / 4;
     const size_t bytes = static_cast<size_t>(cap) * (8 * 9 + 4 * 7) + 16 * 256;
@@ -329,6 +403,11 @@ int build_all_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bin
 // address, so pointers alone do not identify a catalogue).  The fingerprint
 // read synchronises the stream.
 int ensure_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bins* b, cudaStream_t s) {
+  if (h->capturing) {
+    // the geometry must not change between replays; the list cannot be rebuilt inside a graph
+    if (h->pairs_valid && h->key == make_key(cats, n, b)) return LYA_OK;
+    return fail(h, LYA_ERR_INVALID_ARG, "graph capture needs the pair list of these inputs cached (run the call once first)");
+  }
   if (h->pairs_valid && h->key == make_key(cats, n, b)) {
     unsigned long long fp = 0;
     CK(cudaMemcpyAsync(&fp, h->d_fp, 8, cudaMemcpyDeviceToHost, s), "read fingerprint");
@@ -375,6 +454,7 @@ int run_xi(lya_handle* h, const lya_catalog* cats, int ncat, const lya_bins* b, 
     stage_end(h, 0, s);
     h->last = L;
   } else if (prec == LYA_PREC_FP64) {
+    if (h->capturing) return fail(h, LYA_ERR_INVALID_ARG, "the FP64 path allocates: not allowed during graph capture");
     XiLaunch L{};
     stage_begin(h, 0, s);
     CK(launch_xi_fp64(A, cats, ncat, h->dev, h->max_len, b->r_par_max, b->r_perp_max, &L, s),
@@ -430,6 +510,13 @@ int lya_create(lya_handle** out) {
 
 int lya_destroy(lya_handle* h) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (h->capturing) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(h->cap_stream, &g);
+    if (g) cudaGraphDestroy(g);
+    t_capturing = false;
+  }
+  *h->alive = false;   // graphs captured on this handle refuse to launch from now on
   cudaDeviceSynchronize();
   void* bufs[] = {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
                   h->d_err};
@@ -465,6 +552,7 @@ const char* lya_status_string(int s) {
 
 int lya_sync_status(lya_handle* h, void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st = refuse_in_capture(h, "lya_sync_status")) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned flags = 0;
   int st = read_flags(h, s, &flags);
@@ -475,6 +563,7 @@ int lya_sync_status(lya_handle* h, void* stream) {
 int lya_pairs_build(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int64_t* n_pairs,
                     void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_pairs_build")) return st0;
   int st = check_bins(h, bins);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -489,6 +578,7 @@ int lya_pairs_build(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
 int lya_pairs_get(lya_handle* h, int32_t* pair_a, int32_t* pair_b, int64_t cap, int64_t* n_pairs,
                   void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st = refuse_in_capture(h, "lya_pairs_get")) return st;
   if (!h->pairs_valid) return fail(h, LYA_ERR_INVALID_ARG, "no pair list cached");
   if (n_pairs) *n_pairs = h->n_pairs;
   if (cap < h->n_pairs) return fail(h, LYA_ERR_INVALID_ARG, "capacity too small");
@@ -503,6 +593,7 @@ int lya_project(lya_handle* h, const lya_catalog* cat, float* delta_out, void* s
   if (!h) return LYA_ERR_INVALID_ARG;
   if (!delta_out && cat && cat->n_pix > 0) return fail(h, LYA_ERR_INVALID_ARG, "delta_out is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int st0 = check_capture_stream(h, s)) return st0;
   int st = prepare(h, cat, 1, s);
   if (st) return st;
   CK(launch_project(*cat, h->F, 0, delta_out, s), "project");
@@ -516,6 +607,7 @@ int lya_xi(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_prec
   if (st) return st;
   if (!num && !wsum && !xi) return fail(h, LYA_ERR_INVALID_ARG, "no output requested");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = check_capture_stream(h, s))) return st;
   st = prepare(h, cat, 1, s);
   if (st) return st;
   st = ensure_pairs(h, cat, 1, bins, s);
@@ -528,6 +620,7 @@ int lya_xi_pairs(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, ly
                  const int32_t* pair_a, const int32_t* pair_b, int64_t n_pairs, double* num, double* wsum,
                  double* xi, void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_xi_pairs")) return st0;
   int st = check_bins(h, bins);
   if (st) return st;
   if (n_pairs < 0 || (n_pairs > 0 && (!pair_a || !pair_b)))
@@ -572,6 +665,7 @@ int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_et
     return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
   if (eta != LYA_ETA_IDENTITY && eta != LYA_ETA_MEAN_SLOPE) return fail(h, LYA_ERR_INVALID_ARG, "eta");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = check_capture_stream(h, s))) return st;
   st = prepare(h, cat, 1, s);
   if (st) return st;
   st = ensure_pairs(h, cat, 1, bins, s);
@@ -613,6 +707,7 @@ int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
   if (cat && cat->n_pix > 0 && (!grad_delta || !grad_weight))
     return fail(h, LYA_ERR_INVALID_ARG, "gradient output is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = check_capture_stream(h, s))) return st;
   st = prepare(h, cat, 1, s);
   if (st) return st;
   st = ensure_pairs(h, cat, 1, bins, s);
@@ -653,6 +748,7 @@ int lya_xi_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, con
   if (st) return st;
   if (!num && !wsum && !xi) return fail(h, LYA_ERR_INVALID_ARG, "no output requested");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = check_capture_stream(h, s))) return st;
   st = prepare(h, mocks, n_mocks, s);
   if (st) return st;
   st = ensure_pairs(h, mocks, n_mocks, bins, s);
@@ -664,6 +760,7 @@ int lya_xi_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, con
 int lya_autotune(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int32_t* choice,
                  void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_autotune")) return st0;
   int st = check_bins(h, bins);
   if (st) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -731,6 +828,7 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
                    uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
                    void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_pair_stats")) return st0;
   int st = check_bins(h, bins);
   if (st) return st;
   if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
@@ -761,6 +859,7 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
 
 int lya_stage_ms(lya_handle* h, int32_t stage, float* ms) {
   if (!h || !ms || stage < 0 || stage > 3) return LYA_ERR_INVALID_ARG;
+  if (int st = refuse_in_capture(h, "lya_stage_ms")) return st;
   if (!h->ev_used[stage]) return fail(h, LYA_ERR_INVALID_ARG, "stage has not run");
   CK(cudaEventSynchronize(h->ev[stage][1]), "event sync");
   CK(cudaEventElapsedTime(ms, h->ev[stage][0], h->ev[stage][1]), "elapsed");
@@ -771,11 +870,88 @@ int64_t lya_kernel_launches(void) { return static_cast<int64_t>(g_launches.load(
 
 int lya_last_launch(lya_handle* h, int64_t* n_pairs, int32_t* grid, int32_t* block, int32_t* smem_bytes) {
   if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st = refuse_in_capture(h, "lya_last_launch")) return st;
   cudaDeviceSynchronize();
   if (n_pairs) *n_pairs = h->last_pairs;
   if (grid) *grid = h->last.blocks;
   if (block) *block = h->last.warps * 32;
   if (smem_bytes) *smem_bytes = h->last.smem;
+  return LYA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CUDA graph capture of a sequence of calls
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int lya_capture_begin(lya_handle* h, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (h->capturing) return fail(h, LYA_ERR_INVALID_ARG, "a capture is already open on this handle");
+  if (t_capturing) return fail(h, LYA_ERR_INVALID_ARG, "this thread already captures on another handle");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!s) return fail(h, LYA_ERR_INVALID_ARG, "the legacy default stream cannot be captured");
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+  h->capturing = true;
+  h->cap_failed = false;
+  h->cap_stream = s;
+  h->cap_launches0 = g_launches.load();
+  t_capturing = true;
+  return LYA_OK;
+}
+
+int lya_capture_end(lya_handle* h, lya_graph** out) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (out) *out = nullptr;
+  if (!h->capturing) return fail(h, LYA_ERR_INVALID_ARG, "no capture open on this handle");
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  const bool failed = h->cap_failed;
+  h->capturing = false;
+  h->cap_failed = false;
+  t_capturing = false;
+  const long long kernels = g_launches.load() - h->cap_launches0;
+  if (e != cudaSuccess || failed || !out) {
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    if (failed) return fail(h, LYA_ERR_INVALID_ARG, "a call inside the capture failed: " + h->err);
+    return fail(h, LYA_ERR_INVALID_ARG, "out is NULL");
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(h, e2, "instantiate graph");
+  }
+  lya_graph* G = new lya_graph();
+  G->graph = g;
+  G->exec = ex;
+  G->h = h;
+  G->alive = h->alive;
+  G->bufs = handle_buffers(h);
+  G->kernels = kernels;
+  *out = G;
+  return LYA_OK;
+}
+
+int lya_graph_launch(lya_graph* g, void* stream) {
+  if (!g) return LYA_ERR_INVALID_ARG;
+  if (!*g->alive) return LYA_ERR_INVALID_ARG;   // the handle was destroyed
+  lya_handle* h = g->h;
+  if (h->capturing) return fail(h, LYA_ERR_INVALID_ARG, "the handle is capturing");
+  if (handle_buffers(h) != g->bufs)
+    return fail(h, LYA_ERR_INVALID_ARG, "graph is stale: the handle's buffers were reallocated after capture");
+  CK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)), "graph launch");
+  count_launches(g->kernels);
+  return LYA_OK;
+}
+
+int lya_graph_destroy(lya_graph* g) {
+  if (!g) return LYA_ERR_INVALID_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
   return LYA_OK;
 }
 

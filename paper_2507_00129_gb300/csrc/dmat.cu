@@ -126,7 +126,7 @@ constexpr int kCB = 16;   // vectors per batch
 
 // Shared-memory layout of one block (offsets in bytes)
 struct Lay {
-  int U, Wacc, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, gbin, misc, end;
+  int U, Wacc, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, cf, gbin, misc, end;
 };
 
 __host__ __device__ inline int scap_for(int L, int npar, int K) {
@@ -154,6 +154,7 @@ __host__ __device__ inline Lay layout(int L, int scap, int max_len, bool global_
   y.pixa = o; o += al(max_len * 16);
   y.pixb = o; o += al(max_len * 16);
   y.tv = o; o += al(max_len * 8);
+  y.cf = o; o += al(max_len * 16);
   y.gbin = o; o += al(L * 4);
   y.misc = o; o += 64;
   y.end = o;
@@ -179,6 +180,63 @@ __device__ __forceinline__ int local_bin(float2 u, float dj, float cp, float sp,
   const float rt = fmaf(dj, sp, u.y);
   if (rp < fnpar && rt < fnperp) return (static_cast<int>(rt) - t0) * npar + static_cast<int>(rp);
   return -1;
+}
+
+// Tile q of the packed upper triangle of 4 x 4 blocks of the union support:
+// acc = sum over vectors [vlo, vhi) of a a^T + b b^T on that block.
+__device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int scap, int q, int vlo, int vhi,
+                                        float (&acc)[4][4], int* rblk_out, int* cblk_out) {
+  int rr = static_cast<int>((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
+  while (rr * (rr + 1) / 2 > q) --rr;
+  while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
+  const int cblk = rr;                      // column block (>= row block)
+  const int rblk = q - rr * (rr + 1) / 2;   // row block
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  for (int vv = vlo; vv < vhi; ++vv) {
+    const float4 ar = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * rblk);
+    const float4 ac = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * cblk);
+    const float4 br = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * rblk);
+    const float4 bc = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * cblk);
+    const float arv[4] = {ar.x, ar.y, ar.z, ar.w}, acv[4] = {ac.x, ac.y, ac.z, ac.w};
+    const float brv[4] = {br.x, br.y, br.z, br.w}, bcv[4] = {bc.x, bc.y, bc.z, bc.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(brv[u], bcv[v], fmaf(arv[u], acv[v], acc[u][v]));
+  }
+  *rblk_out = rblk;
+  *cblk_out = cblk;
+}
+
+// Subtract a tile from the triangle (entries of the union support S, upper
+// part only), or from G with FP64 atomics for wide pairs.
+template <bool GLOBAL>
+__device__ __forceinline__ void dm_tile_store(const DmArgs& A, float* U, const int32_t* S, const int32_t* gbin,
+                                              int ns, int L, int nbins, int rblk, int cblk,
+                                              const float (&acc)[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = 4 * rblk + u;
+    if (r >= ns) continue;
+    const int lr = S[r];
+    const int rb = tri_rowbase(lr, L);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = 4 * cblk + v;
+      if (c >= ns || c < r) continue;
+      const int lc = S[c];
+      if (!GLOBAL) {
+        U[rb + lc] -= acc[u][v];
+      } else {
+        const int Ar = gbin[lr], Ac = gbin[lc];
+        red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+                           -static_cast<double>(acc[u][v]));
+      }
+    }
+  }
 }
 
 // One forest pair: accumulate its contribution into the triangle (or G).
@@ -209,6 +267,7 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
   int32_t* Vai = reinterpret_cast<int32_t*>(sm + y.Va);   // same storage, fixed point while filling
   int32_t* Vbi = reinterpret_cast<int32_t*>(sm + y.Vb);
   int2* tv = reinterpret_cast<int2*>(sm + y.tv);
+  float4* cf = reinterpret_cast<float4*>(sm + y.cf);
   unsigned char* mark = sm + y.mark;
   int16_t* inv = reinterpret_cast<int16_t*>(sm + y.inv);
   int32_t* S = reinterpret_cast<int32_t*>(sm + y.S);
@@ -257,6 +316,12 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
       }
       for (int k = tid; k < ns_; k += blockDim.x)
         tv[k] = make_int2(__float2int_rn(ps[k].y * scA), __float2int_rn(ps[k].y * ps[k].w * scB));
+      // per vector of this side: rank-1 coefficients and the T weights w_v, w_v y_v
+      const Pix* pv = side == 0 ? pxb : pxa;
+      for (int k = tid; k < nvec; k += blockDim.x) {
+        const Pix me = pv[k];
+        cf[k] = make_float4(sqrtf(me.y * inv_w), sqrtf(me.y * inv_s), me.y, me.y * me.w);
+      }
       __syncthreads();
     }
     const float inv_scA = reinterpret_cast<float*>(misc)[1];
@@ -319,81 +384,54 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
       }
       __syncthreads();
       // T vectors (from unscaled column histograms) and scaling by the
-      // rank-1 coefficients sqrt(w_v / W), sqrt(w_v / S)
-      for (int k = tid; k < ns; k += blockDim.x) {
+      // rank-1 coefficients sqrt(w_v / W), sqrt(w_v / S).  Item (k, vv) =
+      // (bin of S, vector of the batch); the 16 vectors of a bin sit in 16
+      // consecutive lanes, which sum the bin's T terms with shuffles.
+      for (int base = 0; base < ns * kCB; base += blockDim.x) {
+        const int idx = base + tid;
+        const int k = idx / kCB, vv = idx % kCB;
+        const bool act = (k < ns) && (vv < cbn);
         float t1 = 0.f, tx = 0.f, ty = 0.f, txy = 0.f;
-        for (int vv = 0; vv < cbn; ++vv) {
-          const Pix me = side == 0 ? pxb[v0 + vv] : pxa[v0 + vv];
+        if (act) {
+          const float4 c = cf[v0 + vv];
           const float va = static_cast<float>(Vai[vv * scap + k]) * inv_scA;
           const float vb = static_cast<float>(Vbi[vv * scap + k]) * inv_scB;
-          if (side == 0) {
-            t1 = fmaf(me.y, va, t1);
-            tx = fmaf(me.y, vb, tx);
-            ty = fmaf(me.y * me.w, va, ty);
-            txy = fmaf(me.y * me.w, vb, txy);
-          }
-          const float ca = sqrtf(me.y * inv_w);
-          const float cbeta = sqrtf(me.y * inv_s);
-          Va[vv * scap + k] = va * ca;
-          Vb[vv * scap + k] = vb * cbeta;
+          t1 = c.z * va;
+          tx = c.z * vb;
+          ty = c.w * va;
+          txy = c.w * vb;
+          Va[vv * scap + k] = va * c.x;
+          Vb[vv * scap + k] = vb * c.y;
         }
         if (side == 0) {
-          float4 t = T4[S[k]];
-          t.x += t1;
-          t.y += tx;
-          t.z += ty;
-          t.w += txy;
-          T4[S[k]] = t;
+#pragma unroll
+          for (int o = kCB / 2; o > 0; o >>= 1) {
+            t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+            tx += __shfl_xor_sync(0xffffffffu, tx, o);
+            ty += __shfl_xor_sync(0xffffffffu, ty, o);
+            txy += __shfl_xor_sync(0xffffffffu, txy, o);
+          }
+          if (act && vv == 0) {
+            float4 t = T4[S[k]];
+            t.x += t1;
+            t.y += tx;
+            t.z += ty;
+            t.w += txy;
+            T4[S[k]] = t;
+          }
         }
       }
       __syncthreads();
-      // (d) rank-1 updates of the batch: 4 x 4 register tiles of S x S
+      // (d) rank-1 updates of the batch: 4 x 4 register tiles of S x S,
+      // one tile per thread, each adding its 16 entries to the triangle.
       if (eta) {
         const int nt = (ns + 3) >> 2;
         const int ntiles = nt * (nt + 1) / 2;
         for (int q = tid; q < ntiles; q += blockDim.x) {
-          int rr = static_cast<int>((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
-          while (rr * (rr + 1) / 2 > q) --rr;
-          while ((rr + 1) * (rr + 2) / 2 <= q) ++rr;
-          const int cblk = rr;                      // column block (>= row block)
-          const int rblk = q - rr * (rr + 1) / 2;   // row block
           float acc[4][4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-          for (int vv = 0; vv < cbn; ++vv) {
-            const float4 ar = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * rblk);
-            const float4 ac = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * cblk);
-            const float4 br = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * rblk);
-            const float4 bc = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * cblk);
-            const float arv[4] = {ar.x, ar.y, ar.z, ar.w}, acv[4] = {ac.x, ac.y, ac.z, ac.w};
-            const float brv[4] = {br.x, br.y, br.z, br.w}, bcv[4] = {bc.x, bc.y, bc.z, bc.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(brv[u], bcv[v], fmaf(arv[u], acv[v], acc[u][v]));
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = 4 * rblk + u;
-            if (r >= ns) continue;
-            const int lr = S[r];
-            const int rb = tri_rowbase(lr, L);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const int c = 4 * cblk + v;
-              if (c >= ns || c < r) continue;
-              const int lc = S[c];
-              if (!GLOBAL) {
-                U[rb + lc] -= acc[u][v];
-              } else {
-                const int Ar = gbin[lr], Ac = gbin[lc];
-                red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
-                                   -static_cast<double>(acc[u][v]));
-              }
-            }
-          }
+          int rblk, cblk;
+          dm_tile(Va, Vb, scap, q, 0, cbn, acc, &rblk, &cblk);
+          dm_tile_store<GLOBAL>(A, U, S, gbin, ns, L, nbins, rblk, cblk, acc);
         }
       }
       __syncthreads();
@@ -652,7 +690,7 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   {
     const int L = kfit * a.n_par;
     const Lay y = layout(L, scap, max_len, false);
-    LYA_TRY(cudaFuncSetAttribute(dm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, y.end));
+    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<false>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
     LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
                                                                       scap, L, counter);
@@ -661,7 +699,7 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   // wide pairs
   {
     const Lay y = layout(Lw, scapw, max_len, true);
-    LYA_TRY(cudaFuncSetAttribute(dm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, y.end));
+    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<true>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
     LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
                                                                      scapw, Lw, counter);

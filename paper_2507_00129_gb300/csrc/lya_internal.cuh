@@ -214,8 +214,16 @@ struct AdjArgs {
 cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
                         cudaStream_t s);
 
-// scratch helper (api.cu)
+// scratch helper (api.cu).  While the calling thread captures a CUDA graph
+// (lya_capture_begin) it allocates nothing and fails with
+// cudaErrorNotPermitted if the buffer is too small.
 cudaError_t grow(void** p, size_t* cap, size_t need);
+bool capturing_thread();
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `func` on the current
+// device, skipped when a value at least as large was set before (so that a
+// launch captured into a graph needs no attribute call).
+cudaError_t set_max_dynamic_smem(const void* func, int bytes);
 
 // process-wide count of kernel launches (api.cu); LYA_COUNT(n) adds n
 void count_launches(long long n);

@@ -543,8 +543,7 @@ cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps,
   L->grab = grab;
   L->smem = warps * (kAcap * 16 + kHcap * 16 + seg * 16);
   if (L->smem > dev.smem_optin) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(xi_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       L->smem);
+  cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(xi_mixed_kernel), L->smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xi_mixed_kernel, warps * 32, L->smem);
@@ -592,7 +591,7 @@ cudaError_t launch_xi_fp64(const XiArgs& a, const lya_catalog* cats, int n_cats,
   if (seg > 512) seg = 512;
   const int warps = 4;
   const int smem = warps * (kHcap64 * 16 + seg * 32);
-  e = cudaFuncSetAttribute(xi_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = set_max_dynamic_smem(reinterpret_cast<const void*>(xi_fp64_kernel), smem);
   int per_sm = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xi_fp64_kernel, warps * 32, smem);
