@@ -37,6 +37,27 @@ DM_P, DM_SEED = 0.05, 1234
 FLOPS_PER_PAIR = 8  # 4 for the two scaled separations, 2 products, 2 accumulations
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one xi_mixed_kernel launch on the
+# 60,000-forest workload, from one single-pass ncu capture of the full-size launch (summarised in
+# profiles/); keyed by a hash of the kernel's sources and reported only while they are unchanged.
+XI_TRAFFIC = {"sha256": None, "bytes": None}
+
+
+def xi_source_hash() -> str:
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("xi.cu", "lya_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_00129_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def xi_traffic(workload_forests: int):
+    if workload_forests != 60000 or XI_TRAFFIC["sha256"] is None:
+        return None
+    return XI_TRAFFIC["bytes"] if xi_source_hash() == XI_TRAFFIC["sha256"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -331,10 +352,12 @@ def run_ours(args, rank, world, local):
                        step="project + pair list + xi/W mixed + D (5%) + adjoint",
                        seeds=f"catalogue seed 1+rank, DM seed {DM_SEED}"),
         "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
-                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": None,
+                     "unit": "TFLOP/s", "frac": ach / peak_fp32,
+                     "traffic": xi_traffic(args.forests or 60000),
                      "peak_note": f"FP32 FMA peak {n_sm} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz "
                                   f"(sm_max of {how} peaks); {FLOPS_PER_PAIR} algorithmic flops per "
-                                  "in-grid pixel pair"},
+                                  "in-grid pixel pair; traffic = ncu DRAM bytes of one full-size launch "
+                                  "(bytes), null if the kernel changed since"},
         "stages_ms": med, "dominant_stage": dominant,
         "xi_kernel": {"pixel_pairs_per_s": st["pixel_pairs"] / (med["xi"] / 1e3),
                       "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"]},
@@ -525,6 +548,103 @@ def run_desi(args, rank, world, local):
     h.close()
 
 
+def run_mocks(args, rank, world, local):
+    """The mock batch: N independent DESI-like catalogues of 15,000 forests
+    (seeds N*rank .. N*rank+N-1); one step = xi/W of all mocks in one launch
+    + D on a 2% forest-pair subsample of all mocks in one launch."""
+    import torch
+    from paper_2507_00129_gb300 import synth, build
+    build.build()
+    from paper_2507_00129_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nm = args.mocks
+    p_dm, seed_dm = 0.02, 4321
+    t_gen = time.perf_counter()
+    mocks = [api.DeviceCatalog.from_host(synth.make(4, seed=nm * rank + m), device=dev) for m in range(nm)]
+    t_gen = time.perf_counter() - t_gen
+    bins = synth.bins_for(4)
+    nb = bins.nbins
+    h = api.Handle()
+    tune = api.lya_autotune(h, mocks[0], bins)
+    pix = dmpp = 0.0
+    dmpairs = 0
+    for m in mocks:
+        st = api.lya_pair_stats(h, m, bins, 1.0)
+        sd = api.lya_pair_stats(h, m, bins, p_dm, seed_dm)
+        pix += st["pixel_pairs"]
+        dmpp += sd["pixel_pairs_sq"]
+        dmpairs += sd["forest_pairs"]
+    D = torch.empty((nm, nb, nb), dtype=torch.float64, device=dev)
+    Wd = torch.empty((nm, nb), dtype=torch.float64, device=dev)
+
+    def step():
+        n_, w_, x_ = api.lya_xi_batched(h, mocks, bins, "mixed")
+        api.lya_dmat_batched(h, mocks, bins, p_dm, seed_dm, D=D, W=Wd)
+        return n_, w_, x_
+
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        n_, w_, x_ = step()
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    barrier(world)
+    stage = {"xi": [], "dmat": []}
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = api.lya_kernel_launches()
+        e0.record()
+        for _ in range(args.steps):
+            n_, w_, x_ = step()
+            for k in stage:
+                stage[k].append(api.lya_stage_ms(h, k))
+        e1.record()
+        torch.cuda.synchronize()
+        launches = api.lya_kernel_launches() - launches0
+        barrier(world)
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms, pix_total, value = aggregate(ms_local, pix, world)
+    med = {k: float(np.median(v)) for k, v in stage.items()}
+    # per-mock deviation of the batched mixed path from the plain-FP64 path (two mocks)
+    dev_rows = []
+    for m in range(min(2, nm)):
+        _, w64, x64 = api.lya_xi(h, mocks[m], bins, "fp64")
+        W64, X64 = w64.cpu().numpy(), x64.cpu().numpy()
+        Wm, Xm = w_[m].cpu().numpy(), x_[m].cpu().numpy()
+        on = W64 > 0
+        dev_rows.append({"mock": m, "max_rel_dW": float(np.max(np.abs(Wm - W64)[on] / W64[on])),
+                         "max_abs_dxi": float(np.max(np.abs(Xm - X64))), "rms_xi": float(np.sqrt(np.mean(X64 ** 2)))})
+    pk, how = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    ach = FLOPS_PER_PAIR * pix / (med["xi"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"mock_batch_{nm}x15k", "mocks": nm, "forests_per_mock": 15000, "area_deg2": 600,
+                   "bins": "50x50 of 4 Mpc/h", "dm_subsample": p_dm, "grid": "linear 0.8 A, 100-600 px",
+                   "step": "xi/W of all mocks in one launch + D (2%) of all mocks in one launch",
+                   "l2": "inputs larger than L2"},
+        "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
+                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": None},
+        "stages_ms": med,
+        "xi_kernel": {"pixel_pairs_per_s": pix / (med["xi"] / 1e3), "pixel_pairs": pix},
+        "dm": {"pair_pairs_per_s": dmpp / (med["dmat"] / 1e3), "pair_pairs": dmpp, "forest_pairs": dmpairs},
+        "mixed_vs_fp64_per_mock": dev_rows, "first_call_s": first_s, "generate_s": t_gen,
+        "autotune_choice": tune, "gpu_launches": int(launches), "clocks": clk.summary(),
+        "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,8 +655,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--forests", type=int, default=0,
                     help="profiling: use this many forests (same sky density) instead of the workload's")
-    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi"],
-                    help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi")
+    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks"],
+                    help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi; "
+                         "mocks: batch of 15,000-forest mocks, xi/W + D (2%%) in one launch each")
+    ap.add_argument("--mocks", type=int, default=128, help="mocks per rank for --workload mocks")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
     args = ap.parse_args()
     rank, world, local = dist_setup()
@@ -544,6 +666,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "desi":
         run_desi(args, rank, world, local)
+    elif args.workload == "mocks":
+        run_mocks(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -161,6 +161,18 @@ int lya_xi_pairs(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, ly
 int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_eta eta,
              double p_subsample, uint64_t seed, double* dmat, double* wsum_dm, void* stream);
 
+/* Distortion matrices of n_mocks independent catalogues in one launch (the
+ * mock batch used for covariances): mock m gets exactly what lya_dmat gives
+ * for that catalogue alone with the same eta, p_subsample and seed -- the
+ * subsample rule sees forest indices local to each catalogue.  mocks is a
+ * host array of catalogue descriptors (device data each).  dmat:
+ * [n_mocks * nb * nb] float64, mock m at offset m * nb * nb (row A, column B);
+ * wsum_dm (optional): [n_mocks * nb].  The handle's accumulator holds
+ * n_mocks * (nb^2 + nb) doubles.  Pair lists as for lya_xi_batched. */
+int lya_dmat_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, const lya_bins* bins,
+                     lya_eta eta, double p_subsample, uint64_t seed, double* dmat, double* wsum_dm,
+                     void* stream);
+
 /* Gradient of L = sum_A grad_xi[A] xi_A (chain rule of Eq. 2.4):
  *   dL/d delta_i = w_i sum_j gamma_A (w d)_j,
  *   dL/d w_i     = delta_i sum_j gamma_A (w d)_j - sum_j gamma_A xi_A w_j,
@@ -252,7 +264,8 @@ int64_t lya_kernel_launches(void);
  * lya_capture_begin starts a stream capture (thread-local mode) on `stream`,
  * which must not be the legacy default stream (NULL).  Until lya_capture_end,
  * calls of lya_project, lya_xi (MIXED only), lya_xi_batched (MIXED only),
- * lya_dmat and lya_xi_backward on this handle and this stream are recorded,
+ * lya_dmat, lya_dmat_batched and lya_xi_backward on this handle and this
+ * stream are recorded,
  * not run.  While capturing they:
  *  - need the pair list of the same inputs cached (run each call once before
  *    capturing) and skip the geometry check, so ra, dec, dist and offsets

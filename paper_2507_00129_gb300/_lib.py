@@ -57,6 +57,8 @@ SIGNATURES = {
     "lya_xi_pairs": (c_int, [H, CAT, BINS, c_int, c_void_p, c_void_p, c_int64, c_void_p, c_void_p,
                              c_void_p, c_void_p]),
     "lya_dmat": (c_int, [H, CAT, BINS, c_int, c_double, c_uint64, c_void_p, c_void_p, c_void_p]),
+    "lya_dmat_batched": (c_int, [H, CAT, c_int32, BINS, c_int, c_double, c_uint64, c_void_p, c_void_p,
+                                 c_void_p]),
     "lya_xi_backward": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
     "lya_xi_batched": (c_int, [H, CAT, c_int32, BINS, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),

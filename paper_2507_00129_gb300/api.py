@@ -197,6 +197,20 @@ def lya_dmat(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed:
     return D, W
 
 
+def lya_dmat_batched(handle: Handle, mocks: Sequence[DeviceCatalog], bins, p_subsample: float, seed: int,
+                     eta: str = "mean_slope", stream=None, D=None, W=None):
+    nb = bins.n_par * bins.n_perp
+    m = len(mocks)
+    D = torch.empty((m, nb, nb), dtype=torch.float64, device="cuda") if D is None else D
+    W = torch.empty((m, nb), dtype=torch.float64, device="cuda") if W is None else W
+    e = _lib.LYA_ETA_MEAN_SLOPE if eta == "mean_slope" else _lib.LYA_ETA_IDENTITY
+    arr = (LyaCatalog * m)(*[c.c() for c in mocks])
+    b = c_bins(bins)
+    check(handle.h, _lib.load().lya_dmat_batched(handle.h, arr, m, ctypes.byref(b), e, float(p_subsample),
+                                                 ctypes.c_uint64(seed), _ptr(D), _ptr(W), _stream(stream)))
+    return D, W
+
+
 def lya_xi_backward(handle: Handle, cat: DeviceCatalog, bins, grad_xi: torch.Tensor, xi: torch.Tensor,
                     wsum: torch.Tensor, stream=None, grad_delta=None, grad_weight=None):
     gd = torch.empty_like(cat.delta) if grad_delta is None else grad_delta

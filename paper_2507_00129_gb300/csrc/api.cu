@@ -655,27 +655,29 @@ int lya_xi_pairs(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, ly
   return st;
 }
 
-int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_eta eta, double p_subsample,
-             uint64_t seed, double* dmat, double* wsum_dm, void* stream) {
-  if (!h) return LYA_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+int run_dmat_cats(lya_handle* h, const lya_catalog* cats, int n, const lya_bins* bins, lya_eta eta,
+                  double p_subsample, uint64_t seed, double* dmat, double* wsum_dm, cudaStream_t s) {
   int st = check_bins(h, bins);
   if (st) return st;
   if (!dmat) return fail(h, LYA_ERR_INVALID_ARG, "dmat is NULL");
   if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
     return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
   if (eta != LYA_ETA_IDENTITY && eta != LYA_ETA_MEAN_SLOPE) return fail(h, LYA_ERR_INVALID_ARG, "eta");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = check_capture_stream(h, s))) return st;
-  st = prepare(h, cat, 1, s);
+  st = prepare(h, cats, n, s);
   if (st) return st;
-  st = ensure_pairs(h, cat, 1, bins, s);
+  st = ensure_pairs(h, cats, n, bins, s);
   if (st) return st;
   const int nb = bins->n_par * bins->n_perp;
-  const size_t gbytes = static_cast<size_t>(nb) * nb * 8 + static_cast<size_t>(nb) * 8;
+  const size_t gbytes = (static_cast<size_t>(nb) * nb * 8 + static_cast<size_t>(nb) * 8) * n;
   cudaError_t e = grow(&h->gbuf, &h->g_cap, gbytes);
   if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "D accumulator");
   double* G = static_cast<double*>(h->gbuf);
-  double* wdm = G + static_cast<size_t>(nb) * nb;
+  double* wdm = G + static_cast<size_t>(nb) * nb * n;
   DmArgs A;
   A.pairs = static_cast<const int2*>(h->pairbuf);
   A.cs = static_cast<const float2*>(h->csbuf);
@@ -690,11 +692,31 @@ int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_et
   A.G = G;
   A.wdm = wdm;
   A.max_len = h->max_len;
+  A.n_mocks = n;
+  A.fbase = nullptr;
   stage_begin(h, 1, s);
   CK(run_dmat(A, h->dev, &h->scratch2, &h->scratch2_cap, s), "dmat");
   stage_end(h, 1, s);
-  CK(launch_dm_finalize(G, wdm, dmat, wsum_dm, nb, s), "dmat finalize");
+  CK(launch_dm_finalize(G, wdm, dmat, wsum_dm, nb, n, s), "dmat finalize");
   return LYA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lya_dmat(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_eta eta, double p_subsample,
+             uint64_t seed, double* dmat, double* wsum_dm, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  return run_dmat_cats(h, cat, 1, bins, eta, p_subsample, seed, dmat, wsum_dm, static_cast<cudaStream_t>(stream));
+}
+
+int lya_dmat_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, const lya_bins* bins, lya_eta eta,
+                     double p_subsample, uint64_t seed, double* dmat, double* wsum_dm, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (!mocks || n_mocks < 1) return fail(h, LYA_ERR_INVALID_ARG, "no mocks");
+  return run_dmat_cats(h, mocks, n_mocks, bins, eta, p_subsample, seed, dmat, wsum_dm,
+                       static_cast<cudaStream_t>(stream));
 }
 
 int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* grad_xi,

@@ -69,11 +69,15 @@ __global__ void dm_select_kernel(DmArgs A, uint64_t thr, int all, int kfit, int3
        k += (int64_t)gridDim.x * blockDim.x) {
     const int2 p = A.pairs[k];
     int32_t kk = -1;
-    const bool keep = keep_pair(p.x, p.y, A.seed, thr, all);
+    // the subsample rule sees forest indices local to the pair's catalogue,
+    // so a mock's D does not depend on the other mocks of the batch
+    const int m = (p.x >= 0) ? A.F.mock[p.x] : 0;
+    const int base = (p.x >= 0) ? A.fbase[m] : 0;
+    const bool keep = p.x >= 0 && keep_pair(p.x - base, p.y - base, A.seed, thr, all);
     int t_lo, K;
     if (keep && pair_band(A, p.x, p.y, A.cs[k].y, &t_lo, &K)) {
       if (K <= kfit) {
-        kk = t_lo * kfit + (K - 1);
+        kk = (m * A.n_perp + t_lo) * kfit + (K - 1);
         atomicAdd(&count[kk], 1);
       } else {
         const int w = atomicAdd(n_wide, 1);
@@ -105,18 +109,20 @@ struct Chunk {
   int32_t n;
   int32_t t0;
   int32_t K;
+  int32_t mock;    // catalogue whose accumulator the chunk adds to
 };
 
 __global__ void chunk_fill_kernel(const int32_t* count, const int64_t* start, const int64_t* coff,
-                                  int ngroups, int kfit, Chunk* chunks) {
+                                  int ngroups, int kfit, int n_perp, Chunk* chunks) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
     const int c = count[g];
     for (int q = 0; q * kChunk < c; ++q) {
       Chunk ch;
       ch.begin = static_cast<int32_t>(start[g] + q * kChunk);
       ch.n = min(kChunk, c - q * kChunk);
-      ch.t0 = g / kfit;
+      ch.t0 = (g / kfit) % n_perp;
       ch.K = g % kfit + 1;
+      ch.mock = g / (kfit * n_perp);
       chunks[coff[g] + q] = ch;
     }
   }
@@ -174,6 +180,7 @@ __device__ __forceinline__ float word_scale(float B) {
 }
 
 // Bin of pixel pair (i of a, j of b); returns the local bin or -1 if off-grid.
+// The floors are FP32 adds of 2^23 rounded toward -inf, as in the xi kernel.
 __device__ __forceinline__ int local_bin(float2 u, float dj, float cp, float sp, float fnpar, float fnperp,
                                          int npar, int t0) {
   const float rp = fabsf(fmaf(-dj, cp, u.x));
@@ -211,10 +218,12 @@ __device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int sc
   *cblk_out = cblk;
 }
 
-// Subtract a tile from the triangle (entries of the union support S, upper
-// part only), or from G with FP64 atomics for wide pairs.
+// Subtract a tile from the triangle, or from G with FP64 atomics for wide
+// pairs.  Positions r <= c of the union support S (which is in no particular
+// order) cover each unordered pair of its bins once; the symmetric entry goes
+// to (min, max) of the two local bins.
 template <bool GLOBAL>
-__device__ __forceinline__ void dm_tile_store(const DmArgs& A, float* U, const int32_t* S, const int32_t* gbin,
+__device__ __forceinline__ void dm_tile_store(double* G, float* U, const int32_t* S, const int32_t* gbin,
                                               int ns, int L, int nbins, int rblk, int cblk,
                                               const float (&acc)[4][4]) {
 #pragma unroll
@@ -222,17 +231,17 @@ __device__ __forceinline__ void dm_tile_store(const DmArgs& A, float* U, const i
     const int r = 4 * rblk + u;
     if (r >= ns) continue;
     const int lr = S[r];
-    const int rb = tri_rowbase(lr, L);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int c = 4 * cblk + v;
       if (c >= ns || c < r) continue;
       const int lc = S[c];
       if (!GLOBAL) {
-        U[rb + lc] -= acc[u][v];
+        const int lo = min(lr, lc), hi = max(lr, lc);
+        U[tri_rowbase(lo, L) + hi] -= acc[u][v];
       } else {
         const int Ar = gbin[lr], Ac = gbin[lc];
-        red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+        red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
                            -static_cast<double>(acc[u][v]));
       }
     }
@@ -241,7 +250,7 @@ __device__ __forceinline__ void dm_tile_store(const DmArgs& A, float* U, const i
 
 // One forest pair: accumulate its contribution into the triangle (or G).
 template <bool GLOBAL>
-__device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int scap,
+__device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t0, int K, int L, int scap,
                         unsigned char* sm, const Lay& y) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int2 pr = A.pairs[item];
@@ -330,7 +339,8 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
     int cb = kCB;
     while (v0 < nvec) {
       const int cbn = min(cb, nvec - v0);
-      // (a1) mark the local bins the batch touches
+      // (a1) mark the local bins the batch touches (and reset the slot counter of (b))
+      if (tid == 0) misc[3] = 0;
       const int vv_t = tid % cbn;
       const int ostep = blockDim.x / cbn;
       for (int o = tid / cbn; o < nother && tid < ostep * cbn; o += ostep) {
@@ -340,30 +350,33 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
         if (l >= 0) mark[l] = 1;
       }
       __syncthreads();
-      // (b) compaction of the marks into S, inverse map; everyone else clears V
-      if (wid == 0) {
-        int m = 0;
-        for (int l0 = 0; l0 < L; l0 += 32) {
+      // (b) compaction of the marks into S and the inverse map, all warps: a
+      // warp takes 32 local bins, ballots, and reserves its slots in S with
+      // one shared atomic (S is in no particular order; every output entry
+      // still sums its vectors in a fixed order).  V is cleared meanwhile.
+      {
+        const int nwarps = blockDim.x >> 5;
+        for (int l0 = wid * 32; l0 < L; l0 += nwarps * 32) {
           const int l = l0 + lane;
           const bool on = (l < L) && mark[l];
           const unsigned msk = __ballot_sync(0xffffffffu, on);
+          int base = 0;
+          if (lane == 0 && msk) base = atomicAdd(&misc[3], __popc(msk));
+          base = __shfl_sync(0xffffffffu, base, 0);
           if (on) {
-            const int pos = m + __popc(msk & ((1u << lane) - 1u));
+            const int pos = base + __popc(msk & ((1u << lane) - 1u));
             if (pos < scap) S[pos] = l;
             inv[l] = static_cast<int16_t>(pos);
             mark[l] = 0;
           }
-          m += __popc(msk);
         }
-        if (lane == 0) misc[0] = m;
-      } else {
-        for (int k = tid - 32; k < kCB * scap; k += blockDim.x - 32) {
+        for (int k = tid; k < kCB * scap; k += blockDim.x) {
           Va[k] = 0.f;
           Vb[k] = 0.f;
         }
       }
       __syncthreads();
-      const int ns = misc[0];
+      const int ns = misc[3];
       if (ns > scap) {
         // union too large for the staging arrays: retry with half the batch
         __syncthreads();
@@ -431,7 +444,7 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
           float acc[4][4];
           int rblk, cblk;
           dm_tile(Va, Vb, scap, q, 0, cbn, acc, &rblk, &cblk);
-          dm_tile_store<GLOBAL>(A, U, S, gbin, ns, L, nbins, rblk, cblk, acc);
+          dm_tile_store<GLOBAL>(G, U, S, gbin, ns, L, nbins, rblk, cblk, acc);
         }
       }
       __syncthreads();
@@ -452,23 +465,35 @@ __device__ void dm_pair(const DmArgs& A, int item, int t0, int K, int L, int sca
     if (tr.x == 0.f && tr.y == 0.f && tr.z == 0.f && tr.w == 0.f) continue;
     const float f1 = c11 * tr.x, fy = cyy * tr.z, fx = cxx * tr.y, fxy = cxy * tr.w;
     const int rb = tri_rowbase(r, L);
-    for (int c = r + lane; c < L; c += 32) {
+    // two columns per lane per iteration (independent chains)
+    for (int c = r + lane; c < L; c += 64) {
+      const int c2 = c + 32;
       const float4 tc = T4[c];
+      const float4 tc2 = (c2 < L) ? T4[c2] : make_float4(0.f, 0.f, 0.f, 0.f);
       float v = f1 * tc.x + fy * tc.z + fx * tc.y + fxy * tc.w;
+      const float v2 = f1 * tc2.x + fy * tc2.z + fx * tc2.y + fxy * tc2.w;
       if (c == r) v += tr.x;
-      if (v != 0.f) {
-        if (!GLOBAL) {
-          U[rb + c] += v;   // (r, c) owned by this lane
-        } else {
-          const int Ar = gbin[r], Ac = gbin[c];
-          red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+      if (!GLOBAL) {
+        // (r, c), (r, c2) owned by this lane
+        if (v != 0.f) U[rb + c] += v;
+        if (v2 != 0.f) U[rb + c2] += v2;
+      } else {
+        const int Ar = gbin[r];
+        if (v != 0.f) {
+          const int Ac = gbin[c];
+          red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
                              static_cast<double>(v));
+        }
+        if (v2 != 0.f) {
+          const int Ac = gbin[c2];
+          red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+                             static_cast<double>(v2));
         }
       }
     }
     if (lane == 0) {
       if (!GLOBAL) Wacc[r] += tr.x;
-      else red_add_f64_global(A.wdm + gbin[r], static_cast<double>(tr.x));
+      else red_add_f64_global(wdm + gbin[r], static_cast<double>(tr.x));
     }
   }
   __syncthreads();
@@ -510,16 +535,19 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     const long long item = s_item;
     __syncthreads();
     if (item >= n_items) break;
-    int t0, K, first, cnt;
+    int t0, K, first, cnt, mock;
     if (!GLOBAL) {
       const Chunk ch = chunks[item];
-      t0 = ch.t0; K = ch.K; first = ch.begin; cnt = ch.n;
+      t0 = ch.t0; K = ch.K; first = ch.begin; cnt = ch.n; mock = ch.mock;
     } else {
       const int pi = wide[item];
       const int2 p = A.pairs[pi];
       if (!pair_band(A, p.x, p.y, A.cs[pi].y, &t0, &K)) continue;
-      first = 0; cnt = 1;
+      first = 0; cnt = 1; mock = A.F.mock[p.x];
     }
+    // accumulators of the chunk's catalogue
+    double* G = A.G + static_cast<int64_t>(mock) * nbins * nbins;
+    double* wdm = A.wdm + static_cast<int64_t>(mock) * nbins;
     const int L = K * A.n_par;
     for (int k = tid; k < L; k += blockDim.x) {
       const int tt = k / A.n_par, p = k - tt * A.n_par;
@@ -528,7 +556,7 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     __syncthreads();
     for (int q = 0; q < cnt; ++q) {
       const int pi = GLOBAL ? wide[item] : order[first + q];
-      dm_pair<GLOBAL>(A, pi, t0, K, L, scap, sm, y);
+      dm_pair<GLOBAL>(A, G, wdm, pi, t0, K, L, scap, sm, y);
     }
     if (!GLOBAL) {
       // flush the triangle and W of this chunk
@@ -540,7 +568,7 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
           const float v = U[rb + c];
           if (v != 0.f) {
             const int Ac = gbin[c];
-            red_add_f64_global(A.G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
+            red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
                                static_cast<double>(v));
             U[rb + c] = 0.f;
           }
@@ -548,7 +576,7 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
       }
       for (int k = tid; k < L; k += blockDim.x) {
         if (Wacc[k] != 0.f) {
-          red_add_f64_global(A.wdm + gbin[k], static_cast<double>(Wacc[k]));
+          red_add_f64_global(wdm + gbin[k], static_cast<double>(Wacc[k]));
           Wacc[k] = 0.f;
         }
       }
@@ -557,16 +585,27 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
   }
 }
 
-__global__ void dm_finalize_kernel(const double* G, const double* wdm, double* D, double* wout, int nb) {
-  const int64_t n = static_cast<int64_t>(nb) * nb;
+__global__ void dm_finalize_kernel(const double* G, const double* wdm, double* D, double* wout, int nb,
+                                   int n_mocks) {
+  const int64_t nb2 = static_cast<int64_t>(nb) * nb;
+  const int64_t n = nb2 * n_mocks;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int r = static_cast<int>(k / nb), c = static_cast<int>(k - static_cast<int64_t>(r) * nb);
+    const int64_t m = k / nb2, e = k - m * nb2;
+    const int r = static_cast<int>(e / nb), c = static_cast<int>(e - static_cast<int64_t>(r) * nb);
     const int lo = min(r, c), hi = max(r, c);
-    const double w = wdm[r];
-    D[k] = (w != 0.0) ? G[static_cast<int64_t>(lo) * nb + hi] / w : 0.0;
-    if (wout && c == 0) wout[r] = w;
+    const double w = wdm[m * nb + r];
+    D[k] = (w != 0.0) ? G[m * nb2 + static_cast<int64_t>(lo) * nb + hi] / w : 0.0;
+    if (wout && c == 0) wout[m * nb + r] = w;
   }
+}
+
+// first (global) forest index of each catalogue: forests are stored catalogue
+// by catalogue, so it is the forest whose predecessor belongs to another one
+__global__ void fbase_kernel(Forests F, int32_t* fbase) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F.n;
+       f += (int64_t)gridDim.x * blockDim.x)
+    if (f == 0 || F.mock[f] != F.mock[f - 1]) fbase[F.mock[f]] = static_cast<int32_t>(f);
 }
 
 int grid_for(int64_t n, int threads) {
@@ -639,7 +678,9 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
     scap = scap_for(a.n_par, a.n_par, 1);
   }
 
-  const int ngroups = a.n_perp * kfit;
+  const int n_mocks = std::max(a.n_mocks, 1);
+  if (static_cast<int64_t>(n_mocks) * a.n_perp * kfit > (1 << 30)) return cudaErrorInvalidValue;
+  const int ngroups = n_mocks * a.n_perp * kfit;   // (catalogue, first band row, K)
   auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
   const int64_t n = a.n_pairs;
   size_t o = 0;
@@ -652,6 +693,7 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   const size_t o_nch = o; o += al(ngroups * 4);
   const size_t o_coff = o; o += al((ngroups + 1) * 8);
   const size_t o_chunks = o; o += al((n / kChunk + ngroups + 1) * sizeof(Chunk));
+  const size_t o_fbase = o; o += al(static_cast<size_t>(n_mocks) * 4);
   const size_t o_misc = o; o += al(64);
   LYA_TRY(grow(scratch, scratch_cap, o));
   char* sc = static_cast<char*>(*scratch);
@@ -664,25 +706,31 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
   int32_t* nch = reinterpret_cast<int32_t*>(sc + o_nch);
   int64_t* coff = reinterpret_cast<int64_t*>(sc + o_coff);
   Chunk* chunks = reinterpret_cast<Chunk*>(sc + o_chunks);
+  int32_t* fbase = reinterpret_cast<int32_t*>(sc + o_fbase);
   int32_t* misc = reinterpret_cast<int32_t*>(sc + o_misc);   // [0] n_wide, [1] n_chunks
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(sc + o_misc + 16);
 
   LYA_TRY(cudaMemsetAsync(count, 0, ngroups * 4, s));
   LYA_TRY(cudaMemsetAsync(cursor, 0, ngroups * 4, s));
   LYA_TRY(cudaMemsetAsync(misc, 0, 64, s));
-  LYA_TRY(cudaMemsetAsync(a.G, 0, sizeof(double) * nbins * (size_t)nbins, s));
-  LYA_TRY(cudaMemsetAsync(a.wdm, 0, sizeof(double) * nbins, s));
+  LYA_TRY(cudaMemsetAsync(a.G, 0, sizeof(double) * nbins * (size_t)nbins * n_mocks, s));
+  LYA_TRY(cudaMemsetAsync(a.wdm, 0, sizeof(double) * nbins * (size_t)n_mocks, s));
+  LYA_TRY(cudaMemsetAsync(fbase, 0, static_cast<size_t>(n_mocks) * 4, s));
+  if (a.F.n > 0) LYA_COUNT(1), fbase_kernel<<<grid_for(a.F.n, 256), 256, 0, s>>>(a.F, fbase);
+  DmArgs a2 = a;
+  a2.fbase = fbase;
   const int all = a.p_subsample >= 1.0 ? 1 : 0;
   uint64_t thr = 0;
   if (!all && a.p_subsample > 0.0) thr = static_cast<uint64_t>(a.p_subsample * 18446744073709551616.0);
   if (a.p_subsample <= 0.0) return cudaSuccess;  // nothing kept: D = 0, W = 0
   if (n > 0) {
-    LYA_COUNT(1), dm_select_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, thr, all, kfit, key, count, wide, misc);
+    LYA_COUNT(1), dm_select_kernel<<<grid_for(n, 256), 256, 0, s>>>(a2, thr, all, kfit, key, count, wide, misc);
     LYA_COUNT(1), dm_scan_kernel<<<1, 1024, 0, s>>>(count, ngroups, start);
     LYA_COUNT(1), dm_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, key, start, cursor, order);
     LYA_COUNT(1), chunk_count_kernel<<<grid_for(ngroups, 256), 256, 0, s>>>(count, ngroups, nch);
     LYA_COUNT(1), dm_scan_kernel<<<1, 1024, 0, s>>>(nch, ngroups, coff);
-    LYA_COUNT(1), chunk_fill_kernel<<<grid_for(ngroups, 256), 256, 0, s>>>(count, start, coff, ngroups, kfit, chunks);
+    LYA_COUNT(1), chunk_fill_kernel<<<grid_for(ngroups, 256), 256, 0, s>>>(count, start, coff, ngroups, kfit,
+                                                                           a.n_perp, chunks);
     LYA_COUNT(1), to_int32_kernel<<<1, 1, 0, s>>>(coff + ngroups, misc + 1);
     LYA_TRY(cudaGetLastError());
   }
@@ -692,7 +740,7 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
     const Lay y = layout(L, scap, max_len, false);
     LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<false>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
+    LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
                                                                       scap, L, counter);
     LYA_TRY(cudaGetLastError());
   }
@@ -701,7 +749,7 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
     const Lay y = layout(Lw, scapw, max_len, true);
     LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<true>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a, chunks, misc + 1, order, wide, misc,
+    LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
                                                                      scapw, Lw, counter);
     LYA_TRY(cudaGetLastError());
   }
@@ -709,10 +757,10 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
 }
 
 cudaError_t launch_dm_finalize(const double* G, const double* wdm, double* D, double* wdm_out, int nb,
-                               cudaStream_t s) {
-  const int64_t n = static_cast<int64_t>(nb) * nb;
+                               int n_mocks, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(nb) * nb * n_mocks;
   if (n == 0) return cudaSuccess;
-  LYA_COUNT(1), dm_finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(G, wdm, D, wdm_out, nb);
+  LYA_COUNT(1), dm_finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(G, wdm, D, wdm_out, nb, n_mocks);
   return cudaGetLastError();
 }
 

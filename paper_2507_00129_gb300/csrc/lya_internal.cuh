@@ -183,14 +183,16 @@ struct DmArgs {
   int eta_mean_slope;
   double p_subsample;
   uint64_t seed;
-  double* G;        // [nb*nb] upper-triangle accumulator (A <= B)
-  double* wdm;      // [nb]
+  double* G;        // [n_mocks][nb*nb] upper-triangle accumulators (A <= B)
+  double* wdm;      // [n_mocks][nb]
   int max_len;
+  int n_mocks;      // catalogues in the batch (forest f belongs to F.mock[f])
+  const int32_t* fbase;   // [n_mocks] first forest of each catalogue (set by run_dmat)
 };
 cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
                      cudaStream_t s);
 cudaError_t launch_dm_finalize(const double* G, const double* wdm, double* D, double* wdm_out,
-                               int nb, cudaStream_t s);
+                               int nb, int n_mocks, cudaStream_t s);
 
 // adjoint.cu
 struct AdjArgs {

@@ -63,9 +63,9 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
 // memory adds natively; FP32 shared-memory reductions are emulated on this
 // part and far slower.
 __device__ __forceinline__ void split_fixed(float v, float sc16, uint32_t& hi, uint32_t& lo) {
-  const float q = v * sc16;
-  const float hm = __fadd_rd(q, kM15);            // 1.5 * 2^23 + floor(q)
-  const float fr = q - (hm - kM15);               // q - floor(q), exact
+  // q = v * sc16 is exact (sc16 is a power of two) and |q| < 2^21
+  const float hm = __fmaf_rd(v, sc16, kM15);      // 1.5 * 2^23 + floor(q)
+  const float fr = fmaf(v, sc16, kM15 - hm);      // q - floor(q), exact
   const float lm = fmaf(fr, 65536.f, kM15);       // 1.5 * 2^23 + round(fr * 2^16)
   hi = __float_as_uint(hm) - kM15Bits;
   lo = __float_as_uint(lm) - kM15Bits;

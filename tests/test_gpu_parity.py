@@ -259,6 +259,31 @@ def test_batched_equals_single(api, handle):
                                for k in bad[:10]]
 
 
+def test_dmat_batched_equals_single(api, handle):
+    """D of three mocks in one launch equals D of each mock alone (same seed;
+    the subsample rule uses mock-local forest indices), to the FP32 chunk sums'
+    rounding; W^DM likewise.  One mock against the oracle."""
+    bins = synth.bins_for(4)
+    mocks = [synth.make(4, seed=m, n_forests=250) for m in range(3)]
+    dms = [api.DeviceCatalog.from_host(m) for m in mocks]
+    p, seed = 0.3, 77
+    D, W = api.lya_dmat_batched(handle, dms, bins, p, seed)
+    api.lya_sync_status(handle)
+    Db, Wb = _np(D).copy(), _np(W).copy()
+    for m in range(3):
+        D1, W1 = api.lya_dmat(handle, dms[m], bins, p, seed)
+        d1 = _np(D1)
+        np.testing.assert_allclose(Wb[m], _np(W1), rtol=1e-5, atol=1e-9)
+        assert np.all(np.abs(Db[m] - d1) <= 1e-5 * np.abs(d1).max(axis=1, keepdims=True) + 1e-12)
+        assert np.abs(d1).max() > 0.5
+    assert not np.allclose(Db[0], Db[1])
+    pr = oracle.pairs.forest_pairs(mocks[2], bins)
+    sub = oracle.subsample.subsample(pr, seed, p)
+    ref = oracle.dmat.dmat(mocks[2], bins, sub, processes=0, eps_edge=EPS_EDGE)
+    rx = oracle.xi.xi_sums(mocks[2], bins, sub, eps_edge=EPS_EDGE)
+    assert np.all(np.abs(Db[2] - ref["dmat"]) <= _d_allowance(rx, ref) + 1e-12)
+
+
 # ------------------------------------------------------------------ edge cases and errors
 def test_degenerate_catalogues(api, handle):
     from conftest import line_catalog
