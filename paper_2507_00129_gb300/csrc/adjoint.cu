@@ -68,17 +68,28 @@ __global__ void adj_fill_kernel(const int2* pairs, int64_t n, const int64_t* sta
   }
 }
 
-__global__ void chunks_per_forest(Forests F, int32_t* nch) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F.n;
-       f += (int64_t)gridDim.x * blockDim.x)
-    nch[f] = (F.len[f] + 31) / 32;
+// Work items (forest, 32-pixel chunk) are laid out in the order of `order`
+// (forests in HEALPix-cell order, so consecutive items read overlapping
+// neighbour sets from L2), or in index order if it is NULL.
+__device__ __forceinline__ int64_t item_forest(const int32_t* order, int64_t k) {
+  return order ? static_cast<int64_t>(order[k]) : k;
 }
 
-__global__ void item_fill_kernel(Forests F, const int64_t* coff, int2* items) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F.n;
-       f += (int64_t)gridDim.x * blockDim.x) {
+__global__ void chunks_per_forest(Forests F, const int32_t* order, int32_t* nch) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < F.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = item_forest(order, k);
+    nch[k] = (f >= 0) ? (F.len[f] + 31) / 32 : 0;
+  }
+}
+
+__global__ void item_fill_kernel(Forests F, const int32_t* order, const int64_t* coff, int2* items) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < F.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = item_forest(order, k);
+    if (f < 0) continue;
     const int n = (F.len[f] + 31) / 32;
-    for (int c = 0; c < n; ++c) items[coff[f] + c] = make_int2(static_cast<int>(f), c);
+    for (int c = 0; c < n; ++c) items[coff[k] + c] = make_int2(static_cast<int>(f), c);
   }
 }
 
@@ -296,9 +307,9 @@ cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, si
   if (np > 0) LYA_COUNT(1), degree_kernel<<<grid_for(np, 256), 256, 0, s>>>(a.pairs, np, deg);
   LYA_COUNT(1), scan1_kernel<<<1, 1024, 0, s>>>(deg, nf, start);
   if (np > 0) LYA_COUNT(1), adj_fill_kernel<<<grid_for(np, 256), 256, 0, s>>>(a.pairs, np, start, cursor, adj);
-  LYA_COUNT(1), chunks_per_forest<<<grid_for(nf, 256), 256, 0, s>>>(a.F, nch);
+  LYA_COUNT(1), chunks_per_forest<<<grid_for(nf, 256), 256, 0, s>>>(a.F, a.forder, nch);
   LYA_COUNT(1), scan1_kernel<<<1, 1024, 0, s>>>(nch, nf, coff);
-  LYA_COUNT(1), item_fill_kernel<<<grid_for(nf, 256), 256, 0, s>>>(a.F, coff, items);
+  LYA_COUNT(1), item_fill_kernel<<<grid_for(nf, 256), 256, 0, s>>>(a.F, a.forder, coff, items);
   LYA_TRY(cudaGetLastError());
   const int tab_n = (a.n_par + 1) * (a.n_perp + 1);
   int seg = ((std::max(a.max_len, 1) + 31) / 32) * 32;

@@ -124,6 +124,8 @@ struct lya_handle {
   int64_t n_pairs = 0;
   void* csbuf = nullptr;
   size_t cs_cap = 0;
+  void* forder = nullptr;      // forests in HEALPix-cell order (from the pair build), -1 = none
+  size_t forder_cap = 0;
   bool pairs_valid = false;
   CatKey key;
   unsigned long long* d_fp = nullptr;   // geometry fingerprint of the last prepare()
@@ -199,7 +201,7 @@ int check_capture_stream(lya_handle* h, cudaStream_t s) {
 }
 
 std::vector<const void*> handle_buffers(const lya_handle* h) {
-  return {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
+  return {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf, h->forder,
           reinterpret_cast<const void*>(static_cast<uintptr_t>(h->F_capacity)),
           reinterpret_cast<const void*>(static_cast<uintptr_t>(h->pix_cap)),
           reinterpret_cast<const void*>(static_cast<uintptr_t>(h->scratch_cap)),
@@ -368,10 +370,14 @@ int build_all_pairs(lya_handle* h, const lya_catalog* cats, int n, const lya_bin
   PairBuild pbld{nside, b->r_perp_max, th};
   int64_t total = 0, fb = 0;
   int2* pairs = static_cast<int2*>(h->pairbuf);
+  {
+    cudaError_t e = grow(&h->forder, &h->forder_cap, static_cast<size_t>(std::max<int64_t>(h->F.n, 1)) * 4);
+    if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "forest order");
+  }
   for (int m = 0; m < n; ++m) {
     int64_t got = 0;
     CK(build_pairs(h->F, fb, fb + cats[m].n_forests, pbld, &pairs, &h->pair_cap, total, &got,
-                   &h->scratch, &h->scratch_cap, s),
+                   &h->scratch, &h->scratch_cap, static_cast<int32_t*>(h->forder), s),
        "pair list");
     total += got;
     fb += cats[m].n_forests;
@@ -519,7 +525,7 @@ int lya_destroy(lya_handle* h) {
   *h->alive = false;   // graphs captured on this handle refuse to launch from now on
   cudaDeviceSynchronize();
   void* bufs[] = {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
-                  h->d_err};
+                  h->forder, h->d_err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int k = 0; k < 4; ++k)
@@ -752,6 +758,7 @@ int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
   A.grad_delta = grad_delta;
   A.grad_weight = grad_weight;
   A.max_len = h->max_len;
+  A.forder = static_cast<const int32_t*>(h->forder);
   if (cat->n_pix > 0) {
     CK(cudaMemsetAsync(grad_delta, 0, cat->n_pix * 4, s), "zero grad");
     CK(cudaMemsetAsync(grad_weight, 0, cat->n_pix * 4, s), "zero grad");

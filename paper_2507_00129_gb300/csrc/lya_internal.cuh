@@ -128,10 +128,11 @@ struct PairBuild {
   double theta_max;
 };
 // Builds the (a < b) pair list of forests [f0, f1) into *pairs (device buffer
-// grown with cudaMalloc as needed).  Synchronises.
+// grown with cudaMalloc as needed).  Synchronises.  forder (optional, [f0, f1)
+// slots) receives the non-empty forests in HEALPix-cell order, then -1.
 cudaError_t build_pairs(const Forests& F, int64_t f0, int64_t f1, const PairBuild& pb, int2** pairs,
                         int64_t* cap, int64_t pair_base, int64_t* n_out, void** scratch,
-                        size_t* scratch_cap, cudaStream_t s);
+                        size_t* scratch_cap, int32_t* forder, cudaStream_t s);
 cudaError_t launch_pair_geometry(const int2* pairs, int64_t n, Forests F, double inv_dpar,
                                  double inv_dperp, float2* cs, cudaStream_t s);
 cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int2* out,
@@ -212,6 +213,7 @@ struct AdjArgs {
   float* grad_delta;
   float* grad_weight;
   int max_len;
+  const int32_t* forder;   // [F.n] forests in sky order for the work items (-1 = none); NULL = index order
 };
 cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
                         cudaStream_t s);

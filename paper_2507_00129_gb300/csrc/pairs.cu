@@ -149,6 +149,14 @@ __global__ void cell_sort_kernel(const int64_t* start, int64_t ncells, int32_t* 
   }
 }
 
+// order[k] = k-th non-empty forest in cell order (members[0 .. *n_members)), -1 past the end
+__global__ void forder_kernel(const int32_t* members, const int64_t* n_members, int64_t nf, int32_t* order) {
+  const int64_t m = *n_members;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nf;
+       k += (int64_t)gridDim.x * blockDim.x)
+    order[k] = (k < m) ? members[k] : -1;
+}
+
 __global__ void occupied_flags(const int32_t* count, int64_t ncells, int32_t* flag) {
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncells;
        c += (int64_t)gridDim.x * blockDim.x)
@@ -374,9 +382,11 @@ int grid_for(int64_t n, int threads) {
 
 cudaError_t build_pairs(const Forests& F, int64_t f0, int64_t f1, const PairBuild& pb, int2** pairs,
                         int64_t* cap, int64_t pair_base, int64_t* n_out, void** scratch,
-                        size_t* scratch_cap, cudaStream_t s) {
+                        size_t* scratch_cap, int32_t* forder, cudaStream_t s) {
   *n_out = 0;
   const int64_t nf = f1 - f0;
+  // a single forest has no pairs: no order is needed (-1 = no work)
+  if (forder && nf > 0 && nf <= 1) LYA_TRY(cudaMemsetAsync(forder + f0, 0xff, nf * 4, s));
   if (nf <= 1) return cudaSuccess;
   const int64_t ncells = 12LL * pb.nside * pb.nside;
   // scratch layout (bytes, 16-aligned)
@@ -410,6 +420,9 @@ cudaError_t build_pairs(const Forests& F, int64_t f0, int64_t f1, const PairBuil
   LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(count, ncells, start);
   LYA_COUNT(1), scatter_kernel<<<grid_for(nf, kT), kT, 0, s>>>(cell, f0, nf, start, cursor, members);
   LYA_COUNT(1), cell_sort_kernel<<<grid_for(ncells, kT), kT, 0, s>>>(start, ncells, members);
+  // the non-empty forests in cell order (nested HEALPix: neighbours on the sky stay close), kept for
+  // kernels that walk forests and read their neighbours; the rest of the slot stays -1
+  if (forder) LYA_COUNT(1), forder_kernel<<<grid_for(nf, kT), kT, 0, s>>>(members, start + ncells, nf, forder + f0);
   LYA_COUNT(1), occupied_flags<<<grid_for(ncells, kT), kT, 0, s>>>(count, ncells, flag);
   LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(flag, ncells, fpos);
   LYA_COUNT(1), occupied_list<<<grid_for(ncells, kT), kT, 0, s>>>(count, fpos, ncells, occ);
