@@ -339,6 +339,11 @@ def run_ours(args, rank, world, local):
     peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
     dominant = max(med, key=med.get)
+    # FP32-vs-FP64 bin-edge flips of the mixed path on a seeded 1% of the forest pairs
+    flips = api.lya_flip_tally(h, dcp, bins, 0.01, 99)
+    flips["fraction_of_pixel_pairs"] = flips["flipped"] / max(flips["pixel_pairs"], 1)
+    flips["fraction_of_weight"] = flips["flipped_weight"] / max(flips["weight"], 1e-300)
+    flips["sample"] = "forest pairs kept by the subsample rule with p = 0.01, seed 99"
     graph = None if args.no_graph else graph_replay(api, synth, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -365,6 +370,7 @@ def run_ours(args, rank, world, local):
                "pair_pairs": dm["pixel_pairs_sq"], "forest_pairs": dm["forest_pairs"],
                "pixel_pairs": dm["pixel_pairs"]},
         "fp64_path": fp64,
+        "edge_flips": flips,
         "graph_replay": graph,
         "autotune_choice": tune,
         "e2e": {"value": pix_total / e2e_s, "unit": "pixel pairs/s", "h2d_bytes_per_step": h2d,

@@ -213,6 +213,20 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
                    uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
                    void* stream);
 
+/* Tally of the mixed path's bin-edge flips (Section 2.1 binning done with FP32
+ * separations): over the forest pairs kept by the subsample rule of lya_dmat
+ * (p_subsample >= 1 keeps all), every pixel pair is binned with the mixed
+ * kernel's FP32 arithmetic and with the FP64 path's (FP64 distances from
+ * cat->dist, FP64 half-angle).  Host outputs (any may be NULL):
+ * *pixel_pairs = in-grid pixel pairs under FP64 binning, *weight their
+ * sum w_i w_j, *flipped = pixel pairs whose two bins differ (including pairs
+ * in the grid under one binning only), *flipped_weight their sum w_i w_j.
+ * Runs at the device's FP64 rate; use a subsample on large catalogues.
+ * Synchronises. */
+int lya_flip_tally(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample,
+                   uint64_t seed, int64_t* pixel_pairs, int64_t* flipped, double* weight,
+                   double* flipped_weight, void* stream);
+
 /* Device time (ms, CUDA events on the launching stream) of the last run of a
  * stage: 0 = pair kernel of lya_xi / lya_xi_pairs / lya_xi_batched,
  * 1 = distortion-matrix kernels of lya_dmat, 2 = adjoint kernel of
@@ -275,7 +289,8 @@ int64_t lya_kernel_launches(void);
  *    LYA_ERR_INVALID_ARG (again: run the same calls once before capturing);
  *  - fail with LYA_ERR_INVALID_ARG if they would synchronise (lya_sync_status,
  *    lya_pairs_build, lya_pairs_get, lya_xi_pairs, lya_autotune,
- *    lya_pair_stats, lya_stage_ms, lya_last_launch) or use another stream.
+ *    lya_pair_stats, lya_flip_tally, lya_stage_ms, lya_last_launch) or use
+ *    another stream.
  * Input checks still run on the device at every replay; read them with
  * lya_sync_status after a replay.  Outputs (caller pointers and the handle's
  * scratch) are fixed at capture.

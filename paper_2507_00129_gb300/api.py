@@ -262,6 +262,17 @@ def lya_pair_stats(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float 
     return {"forest_pairs": n.value, "pixel_pairs": pix.value, "pixel_pairs_sq": sq.value}
 
 
+def lya_flip_tally(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float = 1.0, seed: int = 0,
+                   stream=None):
+    n, f = ctypes.c_int64(), ctypes.c_int64()
+    w, wf = ctypes.c_double(), ctypes.c_double()
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_flip_tally(handle.h, ctypes.byref(c), ctypes.byref(b), float(p_subsample),
+                                               ctypes.c_uint64(seed), ctypes.byref(n), ctypes.byref(f),
+                                               ctypes.byref(w), ctypes.byref(wf), _stream(stream)))
+    return {"pixel_pairs": n.value, "flipped": f.value, "weight": w.value, "flipped_weight": wf.value}
+
+
 STAGES = {"xi": 0, "dmat": 1, "adjoint": 2, "pairs": 3}
 
 

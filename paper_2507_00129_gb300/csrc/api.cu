@@ -886,6 +886,41 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
   return LYA_OK;
 }
 
+int lya_flip_tally(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample, uint64_t seed,
+                   int64_t* pixel_pairs, int64_t* flipped, double* weight, double* flipped_weight, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_flip_tally")) return st0;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
+    return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  XiArgs A{};
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  FlipOut* dout = reinterpret_cast<FlipOut*>(h->d_u64 + 1);
+  CK(launch_flip_tally(A, cat->dist, bins->n_par / bins->r_par_max, bins->n_perp / bins->r_perp_max, p_subsample,
+                       seed, dout, h->dev, s),
+     "flip tally");
+  FlipOut host{};
+  CK(cudaMemcpyAsync(&host, dout, sizeof(FlipOut), cudaMemcpyDeviceToHost, s), "read tally");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (pixel_pairs) *pixel_pairs = static_cast<int64_t>(host.pix);
+  if (flipped) *flipped = static_cast<int64_t>(host.flips);
+  if (weight) *weight = host.w;
+  if (flipped_weight) *flipped_weight = host.wflip;
+  return LYA_OK;
+}
+
 int lya_stage_ms(lya_handle* h, int32_t stage, float* ms) {
   if (!h || !ms || stage < 0 || stage > 3) return LYA_ERR_INVALID_ARG;
   if (int st = refuse_in_capture(h, "lya_stage_ms")) return st;

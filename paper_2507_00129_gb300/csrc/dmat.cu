@@ -343,6 +343,8 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
       if (tid == 0) misc[3] = 0;
       const int vv_t = tid % cbn;
       const int ostep = blockDim.x / cbn;
+      // independent items: unrolled so that several items' loads are in flight
+#pragma unroll 4
       for (int o = tid / cbn; o < nother && tid < ostep * cbn; o += ostep) {
         const int i = side == 0 ? o : v0 + vv_t;
         const int j = side == 0 ? v0 + vv_t : o;
@@ -384,6 +386,8 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
         continue;
       }
       // (a2) dense histograms on S
+      // independent items: unrolled so that several items' loads are in flight
+#pragma unroll 4
       for (int o = tid / cbn; o < nother && tid < ostep * cbn; o += ostep) {
         const int i = side == 0 ? o : v0 + vv_t;
         const int j = side == 0 ? v0 + vv_t : o;

@@ -239,6 +239,16 @@ struct StatsOut {
   unsigned long long pix;
   unsigned long long pix_sq;
 };
+// xi.cu: FP32-vs-FP64 bin-edge flips over the kept pairs
+struct FlipOut {
+  unsigned long long pix;     // in-grid pixel pairs under FP64 binning
+  unsigned long long flips;   // pixel pairs whose FP32 bin differs (in grid or not)
+  double w;                   // their weights
+  double wflip;
+};
+cudaError_t launch_flip_tally(const XiArgs& a, const double* dist, double inv_dpar, double inv_dperp,
+                              double p_subsample, uint64_t seed, FlipOut* out, const DevInfo& dev,
+                              cudaStream_t s);
 cudaError_t launch_pair_stats(const XiArgs& a, double p_subsample, uint64_t seed, StatsOut* out,
                               const DevInfo& dev, cudaStream_t s);
 

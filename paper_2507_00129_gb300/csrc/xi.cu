@@ -12,13 +12,16 @@
 //        r_perp/D =   d~_j *   s/D  + ((d~_i * s/D) + (ref_a + ref_b) s/D)
 //  * floor() is an FP32 add rounded toward -inf of 2^23 (the integer lands in
 //    the low mantissa bits), so the bin index needs no float->int conversion;
-//  * the histogram is warp private and covers only the rows t of the pair's
-//    r_perp band (r_perp is monotone in both distances, so the band follows
-//    from the extreme pixels); products are FP32 and shared-memory float
-//    atomics accumulate one 32-pixel chunk of forest a (at most 32 x n_b
-//    terms per bin), which is then folded into a warp-private FP64 band
-//    accumulator; after the forest pair the FP64 band is added to the bin sums
-//    in global memory with FP64 atomics (skipping empty bins);
+//  * each lane walks j and keeps the current bin's run sums in registers; when
+//    the bin changes the run goes to the warp's chunk histogram, which covers
+//    only the rows of the pair's r_perp band, as exact two-word fixed point
+//    summed with native 32-bit shared-memory reductions (every lane issues
+//    them every step, aimed at its own dummy word when its run goes on);
+//  * every two 32-pixel chunks of forest a the integer sums are folded into a
+//    warp-private compensated FP32 (TwoSum) band accumulator, which survives
+//    across consecutive pairs with the same first band row (the pair list is
+//    ordered for this) and is added to the FP64 bin sums in global memory when
+//    the band changes;
 //  * the j loop of each 32-pixel chunk of a is restricted to the pixels that
 //    can be in range (distances are sorted; two binary searches).
 // FP64 kernel (LYA_PREC_FP64): the same decomposition with FP64 distances,
@@ -520,6 +523,77 @@ __global__ void pair_stats_kernel(XiArgs A, uint64_t seed, uint64_t thr, int all
   }
 }
 
+// Bin-edge flips of the mixed path: for every pixel pair of the kept forest
+// pairs, the bin from the mixed kernel's FP32 arithmetic against the bin from
+// the FP64 path's arithmetic (FP64 distances of the caller's catalogue, FP64
+// half-angle from the unit vectors).  One warp per forest pair.
+__global__ void flip_tally_kernel(XiArgs A, const double* dist, double inv_dpar, double inv_dperp,
+                                  uint64_t seed, uint64_t thr, int all, FlipOut* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int npar = A.n_par, nperp = A.n_perp;
+  const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(nperp);
+  unsigned long long n64 = 0, nflip = 0;
+  double w64 = 0.0, wflip = 0.0;
+  for (int64_t k = warp; k < A.n_pairs; k += nw) {
+    const int2 ab = A.pairs[k];
+    if (ab.x < 0 || !keep_pair(ab.x, ab.y, seed, thr, all)) continue;
+    const int a = ab.x, b = ab.y;
+    const int na = A.F.len[a], nb = A.F.len[b];
+    if (na == 0 || nb == 0) continue;
+    const float cp = A.cs[k].x, sp = A.cs[k].y;
+    const float refa = A.F.dref[a], refb = A.F.dref[b];
+    const float Dc = (refa - refb) * cp, Ds = (refa + refb) * sp;
+    const Pix* pa = A.pix + A.F.off[a];
+    const Pix* pb = A.pix + A.F.off[b];
+    const double* da = dist + A.F.off[a];
+    const double* db = dist + A.F.off[b];
+    const double sx = A.F.ux[a] + A.F.ux[b], sy = A.F.uy[a] + A.F.uy[b], sz = A.F.uz[a] + A.F.uz[b];
+    const double dx = A.F.ux[a] - A.F.ux[b], dy = A.F.uy[a] - A.F.uy[b], dz = A.F.uz[a] - A.F.uz[b];
+    const double cp64 = 0.5 * sqrt(sx * sx + sy * sy + sz * sz) * inv_dpar;
+    const double sp64 = 0.5 * sqrt(dx * dx + dy * dy + dz * dz) * inv_dperp;
+    for (int i = lane; i < na; i += 32) {
+      const Pix pi = pa[i];
+      const double di = da[i];
+      const float uc = fmaf(pi.x, cp, Dc), us = fmaf(pi.x, sp, Ds);
+      for (int j = 0; j < nb; ++j) {
+        const Pix q = pb[j];
+        const float rp = fabsf(fmaf(-q.x, cp, uc));
+        const float rt = fmaf(q.x, sp, us);
+        const int bin32 = (rp < fnpar && rt < fnperp)
+                              ? static_cast<int>(__float_as_uint(__fadd_rd(rp, kMagic)) - kMagicBits) * nperp +
+                                    static_cast<int>(__float_as_uint(__fadd_rd(rt, kMagic)) - kMagicBits)
+                              : -1;
+        const double x = fabs(di - db[j]) * cp64;
+        const double y = (di + db[j]) * sp64;
+        const int bin64 = (x < npar && y < nperp) ? static_cast<int>(x) * nperp + static_cast<int>(y) : -1;
+        const double w = static_cast<double>(pi.y) * static_cast<double>(q.y);
+        if (bin64 >= 0) {
+          n64 += 1;
+          w64 += w;
+        }
+        if (bin32 != bin64) {
+          nflip += 1;
+          wflip += w;
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+    nflip += __shfl_xor_sync(0xffffffffu, nflip, o);
+    w64 += __shfl_xor_sync(0xffffffffu, w64, o);
+    wflip += __shfl_xor_sync(0xffffffffu, wflip, o);
+  }
+  if (lane == 0 && n64 + nflip > 0) {
+    atomicAdd(&out->pix, n64);
+    atomicAdd(&out->flips, nflip);
+    atomicAdd(&out->w, w64);
+    atomicAdd(&out->wflip, wflip);
+  }
+}
+
 __global__ void finalize_kernel(const double* num, const double* wsum, double* xi, int64_t n) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -621,6 +695,17 @@ cudaError_t launch_pair_stats(const XiArgs& a, double p_subsample, uint64_t seed
   const int all = p_subsample >= 1.0 ? 1 : 0;
   const uint64_t thr = all ? 0 : static_cast<uint64_t>(p_subsample * 18446744073709551616.0);
   LYA_COUNT(1), pair_stats_kernel<<<dev.sms * 8, 256, 0, s>>>(a, seed, thr, all, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flip_tally(const XiArgs& a, const double* dist, double inv_dpar, double inv_dperp,
+                              double p_subsample, uint64_t seed, FlipOut* out, const DevInfo& dev,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(FlipOut), s);
+  if (e != cudaSuccess || a.n_pairs == 0 || p_subsample <= 0.0) return e;
+  const int all = p_subsample >= 1.0 ? 1 : 0;
+  const uint64_t thr = all ? 0 : static_cast<uint64_t>(p_subsample * 18446744073709551616.0);
+  LYA_COUNT(1), flip_tally_kernel<<<dev.sms * 8, 256, 0, s>>>(a, dist, inv_dpar, inv_dperp, seed, thr, all, out);
   return cudaGetLastError();
 }
 

@@ -98,6 +98,25 @@ def test_xi_mixed_matches_oracle_within_edge_allowance(api, handle, c0, ref0):
     assert dW.sum() <= 0.05 * ref0["edge_w"].sum() + 1e-6 * ref0["wsum"].sum()
 
 
+def test_flip_tally_is_bounded_by_edge_mass(api, handle, c0, ref0):
+    """The pixel pairs whose FP32 bin differs from their FP64 bin carry at most
+    the oracle's edge mass for eps = 6e-5; the FP64 in-grid count is the
+    oracle's, and the mixed and FP64 weights differ by at most the flipped
+    weight moved out of one bin and into another."""
+    cat, bins, _ = c0
+    dc = api.DeviceCatalog.from_host(cat)
+    t = api.lya_flip_tally(handle, dc, bins, 1.0)
+    n_ref = float(ref0["count"].sum())
+    assert abs(t["pixel_pairs"] - n_ref) <= 1e-6 * n_ref
+    np.testing.assert_allclose(t["weight"], ref0["wsum"].sum(), rtol=1e-6)
+    assert 0 <= t["flipped_weight"] <= ref0["edge_w"].sum() + 1e-9
+    assert t["flipped"] <= 1e-3 * t["pixel_pairs"]
+    _, w_mixed, _ = api.lya_xi(handle, dc, bins, "mixed")
+    _, w_fp64, _ = api.lya_xi(handle, dc, bins, "fp64")
+    moved = float(np.abs(_np(w_mixed) - _np(w_fp64)).sum())
+    assert moved <= 2 * t["flipped_weight"] + 1e-9 * float(_np(w_fp64).sum())
+
+
 def test_xi_pairs_subset_equals_oracle(api, handle, c0):
     cat, bins, pr = c0
     rng = np.random.default_rng(11)
