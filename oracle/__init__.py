@@ -15,8 +15,9 @@ Contents (each function cites the passage it follows):
 * ``dmat``      -- distortion matrix D_AB, Eq. (2.6): literal and expanded forms
 * ``subsample`` -- the seeded forest-pair subsample used for D    (Section 2.2)
 * ``adjoint``   -- gradient of L = sum_A c_A xi_A w.r.t. delta and w (chain rule of Eq. 2.4)
+* ``covariance``-- HEALPix sub-samples and the weighted sub-sample covariance of xi
 
 Everything is float64.  Readings of passages the paper leaves open are listed
 in the module docstrings.
 """
-from . import geometry, pairs, xi, project, dmat, subsample, adjoint  # noqa: F401
+from . import geometry, pairs, xi, project, dmat, subsample, adjoint, covariance  # noqa: F401
