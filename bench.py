@@ -344,6 +344,17 @@ def run_ours(args, rank, world, local):
     flips["fraction_of_pixel_pairs"] = flips["flipped"] / max(flips["pixel_pairs"], 1)
     flips["fraction_of_weight"] = flips["flipped_weight"] / max(flips["weight"], 1e-300)
     flips["sample"] = "forest pairs kept by the subsample rule with p = 0.01, seed 99"
+    # covariance from HEALPix sub-samples (nside 8, the data split of the paper's inputs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    n_s, w_s, _, _ = api.lya_xi_subsamples(h, dcp, bins, 8)
+    ev[1].record()
+    cov, _ = api.lya_xi_covariance(h, n_s, w_s)
+    ev[2].record()
+    torch.cuda.synchronize()
+    covariance = {"nside": 8, "subsamples_with_pairs": int((w_s.sum(dim=1) > 0).sum()),
+                  "subsample_xi_ms": ev[0].elapsed_time(ev[1]), "covariance_ms": ev[1].elapsed_time(ev[2])}
+    del n_s, w_s, cov
     graph = None if args.no_graph else graph_replay(api, synth, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -371,6 +382,7 @@ def run_ours(args, rank, world, local):
                "pixel_pairs": dm["pixel_pairs"]},
         "fp64_path": fp64,
         "edge_flips": flips,
+        "covariance": covariance,
         "graph_replay": graph,
         "autotune_choice": tune,
         "e2e": {"value": pix_total / e2e_s, "unit": "pixel pairs/s", "h2d_bytes_per_step": h2d,

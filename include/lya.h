@@ -213,6 +213,28 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
                    uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
                    void* stream);
 
+/* Per sub-sample sums for a covariance of xi (the paper takes its
+ * uncertainties from sub-samples of the forests in HEALPix pixels, Sections
+ * 3.2 and 3.4): forest pair (a < b) is added to the sub-sample of its first
+ * forest a, the nested HEALPix pixel at resolution nside (a power of two,
+ * 1..64) containing a's line of sight.  Outputs [12 nside^2 * nb] float64,
+ * sub-sample s at offset s * nb: num and wsum (required; the sums of lya_xi
+ * over the sub-sample's pairs, MIXED precision), xi (optional, num / wsum).
+ * sub_of_forest (optional, device [n_forests] int32) receives each forest's
+ * sub-sample.  Summing over sub-samples gives lya_xi's num and wsum. */
+int lya_xi_subsamples(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int32_t nside,
+                      double* num, double* wsum, double* xi, int32_t* sub_of_forest, void* stream);
+
+/* Weighted sub-sample covariance of xi from per sub-sample sums (device
+ * [n_sub * n_bins] float64 each, sub-sample s at offset s * n_bins):
+ *   C_AB = sum_s W^s_A W^s_B (xi^s_A - xi_A)(xi^s_B - xi_B) / (W_A W_B),
+ * xi^s = N^s / W^s, W = sum_s W^s, xi = (sum_s N^s) / W; rows and columns
+ * with W_A = 0 are zero.  cov: [n_bins * n_bins] float64 (row A, column B);
+ * xi (optional): [n_bins] full-sample xi.  FP64; sub-samples without weight
+ * are skipped.  Limits: n_bins <= 65536, n_sub <= 2^20. */
+int lya_xi_covariance(lya_handle* h, const double* num_sub, const double* wsum_sub, int32_t n_sub,
+                      int32_t n_bins, double* cov, double* xi, void* stream);
+
 /* Tally of the mixed path's bin-edge flips (Section 2.1 binning done with FP32
  * separations): over the forest pairs kept by the subsample rule of lya_dmat
  * (p_subsample >= 1 keeps all), every pixel pair is binned with the mixed

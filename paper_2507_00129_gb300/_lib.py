@@ -67,6 +67,8 @@ SIGNATURES = {
                                 POINTER(c_int32)]),
     "lya_pair_stats": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
                                POINTER(c_double), c_void_p]),
+    "lya_xi_subsamples": (c_int, [H, CAT, BINS, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lya_xi_covariance": (c_int, [H, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "lya_flip_tally": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
                                POINTER(c_double), POINTER(c_double), c_void_p]),
     "lya_stage_ms": (c_int, [H, c_int32, POINTER(ctypes.c_float)]),

@@ -262,6 +262,33 @@ def lya_pair_stats(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float 
     return {"forest_pairs": n.value, "pixel_pairs": pix.value, "pixel_pairs_sq": sq.value}
 
 
+def lya_xi_subsamples(handle: Handle, cat: DeviceCatalog, bins, nside: int, stream=None):
+    """Per sub-sample (nested HEALPix pixel of the first forest) num, wsum, xi
+    as [12 nside^2, nb] tensors, and each forest's sub-sample."""
+    nb = bins.n_par * bins.n_perp
+    ns = 12 * nside * nside
+    num = torch.empty((ns, nb), dtype=torch.float64, device="cuda")
+    wsum = torch.empty_like(num)
+    xi = torch.empty_like(num)
+    sub = torch.empty(max(cat.n_forests, 1), dtype=torch.int32, device="cuda")
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_subsamples(handle.h, ctypes.byref(c), ctypes.byref(b), int(nside), _ptr(num),
+                                                  _ptr(wsum), _ptr(xi), _ptr(sub), _stream(stream)))
+    return num, wsum, xi, sub[: cat.n_forests]
+
+
+def lya_xi_covariance(handle: Handle, num_sub: torch.Tensor, wsum_sub: torch.Tensor, stream=None):
+    """Weighted sub-sample covariance [nb, nb] and the full-sample xi [nb]."""
+    ns, nb = num_sub.shape
+    cov = torch.empty((nb, nb), dtype=torch.float64, device="cuda")
+    xi = torch.empty(nb, dtype=torch.float64, device="cuda")
+    n = num_sub.to(torch.float64).contiguous()
+    w = wsum_sub.to(torch.float64).contiguous()
+    check(handle.h, _lib.load().lya_xi_covariance(handle.h, _ptr(n), _ptr(w), int(ns), int(nb), _ptr(cov), _ptr(xi),
+                                                  _stream(stream)))
+    return cov, xi
+
+
 def lya_flip_tally(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float = 1.0, seed: int = 0,
                    stream=None):
     n, f = ctypes.c_int64(), ctypes.c_int64()

@@ -921,6 +921,46 @@ int lya_flip_tally(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
   return LYA_OK;
 }
 
+int lya_xi_subsamples(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, int32_t nside, double* num,
+                      double* wsum, double* xi, int32_t* sub_of_forest, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (nside < 1 || nside > 64 || (nside & (nside - 1)))
+    return fail(h, LYA_ERR_INVALID_ARG, "nside must be a power of two in 1..64");
+  if (!num || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "num and wsum are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = check_capture_stream(h, s))) return st;
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  // the pair kernel adds forest pair (a, b) at offset F.mock[a] * nb: the
+  // sub-sample of the first forest (prepare() resets F.mock on the next call)
+  CK(launch_subsample_ids(h->F, nside, h->F.mock, s), "sub-sample ids");
+  if (sub_of_forest && cat->n_forests > 0)
+    CK(cudaMemcpyAsync(sub_of_forest, h->F.mock, static_cast<size_t>(cat->n_forests) * 4, cudaMemcpyDeviceToDevice,
+                       s),
+       "sub-sample ids out");
+  const int n_sub = 12 * nside * nside;
+  return run_xi(h, cat, n_sub, bins, LYA_PREC_MIXED, static_cast<const int2*>(h->pairbuf),
+                static_cast<const float2*>(h->csbuf), h->n_pairs, num, wsum, xi, s);
+}
+
+int lya_xi_covariance(lya_handle* h, const double* num_sub, const double* wsum_sub, int32_t n_sub, int32_t n_bins,
+                      double* cov, double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (n_sub < 1 || n_bins < 1 || n_bins > 65536 || n_sub > (1 << 20))
+    return fail(h, LYA_ERR_INVALID_ARG, "n_sub in 1..2^20 and n_bins in 1..65536 required");
+  if (!num_sub || !wsum_sub || !cov) return fail(h, LYA_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int st = check_capture_stream(h, s)) return st;
+  cudaError_t e = grow(&h->outbuf, &h->out_cap, covariance_scratch_bytes(n_sub, n_bins));
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "covariance scratch");
+  CK(launch_covariance(num_sub, wsum_sub, n_sub, n_bins, cov, xi, h->outbuf, s), "covariance");
+  return LYA_OK;
+}
+
 int lya_stage_ms(lya_handle* h, int32_t stage, float* ms) {
   if (!h || !ms || stage < 0 || stage > 3) return LYA_ERR_INVALID_ARG;
   if (int st = refuse_in_capture(h, "lya_stage_ms")) return st;

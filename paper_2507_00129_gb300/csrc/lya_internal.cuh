@@ -142,6 +142,14 @@ cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int
 cudaError_t sort_pairs_by_band(int2* pairs, float2* cs, int64_t n, Forests F, const Pix* pix, int n_perp,
                                int n_mocks, void** scratch, size_t* scratch_cap, cudaStream_t s);
 cudaError_t launch_unpack_pairs(const int2* p, int64_t n, int32_t* a, int32_t* b, cudaStream_t s);
+// id[f] = nested HEALPix pixel (resolution nside) of forest f's line of sight (0 for empty forests)
+cudaError_t launch_subsample_ids(const Forests& F, int nside, int32_t* id, cudaStream_t s);
+
+// cov.cu: weighted sub-sample covariance from per sub-sample sums [n_sub][nb]
+// (scratch: 3 nb doubles + n_sub + 1 ints, 256-byte aligned)
+size_t covariance_scratch_bytes(int n_sub, int nb);
+cudaError_t launch_covariance(const double* num_s, const double* wsum_s, int n_sub, int nb, double* cov,
+                              double* xi_out, void* scratch, cudaStream_t s);
 
 // xi.cu
 struct XiLaunch {

@@ -95,6 +95,18 @@ __global__ void cell_kernel(Forests F, int64_t f0, int64_t nf, int nside, int32_
   }
 }
 
+// sub-sample of each forest: the nested HEALPix pixel of its line of sight
+__global__ void subsample_id_kernel(Forests F, int nside, int32_t* id) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F.n;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    double phi = atan2(F.uy[f], F.ux[f]);
+    if (phi < 0) phi += 2.0 * M_PI;
+    if (phi >= 2.0 * M_PI) phi = 0.0;
+    const double z = fmin(1.0, fmax(-1.0, F.uz[f]));
+    id[f] = (F.len[f] > 0) ? static_cast<int32_t>(ang2pix_nest(nside, z, phi)) : 0;
+  }
+}
+
 // exclusive scan of n int32 counts into n+1 int64 offsets, one block
 __global__ void scan_kernel(const int32_t* in, int64_t n, int64_t* out) {
   __shared__ int64_t part[1024];
@@ -535,6 +547,12 @@ cudaError_t sort_pairs_by_band(int2* pairs, float2* cs, int64_t n, Forests F, co
   LYA_TRY(cudaMemcpyAsync(pairs, p2, n * 8, cudaMemcpyDeviceToDevice, s));
   LYA_TRY(cudaMemcpyAsync(cs, c2, n * 8, cudaMemcpyDeviceToDevice, s));
   return cudaSuccess;
+}
+
+cudaError_t launch_subsample_ids(const Forests& F, int nside, int32_t* id, cudaStream_t s) {
+  if (F.n == 0) return cudaSuccess;
+  LYA_COUNT(1), subsample_id_kernel<<<grid_for(F.n, kT), kT, 0, s>>>(F, nside, id);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_pairs(const int32_t* a, const int32_t* b, int64_t n, int2* out,
