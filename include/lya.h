@@ -137,7 +137,9 @@ int lya_project(lya_handle* h, const lya_catalog* cat, float* delta_out, void* s
  * list.  num[A] = sum (w d)_i (w d)_j, wsum[A] = sum w_i w_j, xi = num/wsum
  * (0 where wsum = 0), each [n_par*n_perp] float64, A = p*n_perp + t.
  * Any of num/wsum/xi may be NULL except that xi needs num and wsum.
- * Builds the pair list (synchronising) if none is cached for these inputs. */
+ * Builds the pair list (synchronising) if none is cached for these inputs.
+ * Bin-grid limit of the pair kernels: n_par <= 203 (MIXED), <= 256 (FP64);
+ * beyond it LYA_ERR_TOO_LARGE. */
 int lya_xi(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, lya_precision prec,
            double* num, double* wsum, double* xi, void* stream);
 

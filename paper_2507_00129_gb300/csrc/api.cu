@@ -450,6 +450,10 @@ int run_xi(lya_handle* h, const lya_catalog* cats, int ncat, const lya_bins* b, 
   A.wsum = W;
   A.nb = nb;
   A.counter = h->d_counter;
+  if (prec == LYA_PREC_MIXED && b->n_par > 203)
+    return fail(h, LYA_ERR_TOO_LARGE, "the mixed path supports n_par <= 203");
+  if (prec == LYA_PREC_FP64 && b->n_par > 256)
+    return fail(h, LYA_ERR_TOO_LARGE, "the FP64 path supports n_par <= 256");
   if (prec == LYA_PREC_MIXED) {
     XiLaunch L;
     const int warps = (h->tuned_for_npar == b->n_par) ? h->tuned_warps : 8;
@@ -798,7 +802,7 @@ int lya_autotune(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, in
   st = ensure_pairs(h, cat, 1, bins, s);
   if (st) return st;
   // candidate (warps per block, pairs per work grab)
-  static const int cand[][2] = {{8, 1}, {8, 4}, {8, 16}, {4, 4}, {16, 4}, {12, 4}};
+  static const int cand[][2] = {{8, 1}, {8, 4}, {8, 16}, {4, 4}, {16, 4}, {12, 4}, {13, 4}, {14, 4}, {13, 2}};
   const int nc = sizeof(cand) / sizeof(cand[0]);
   const int nb = bins->n_par * bins->n_perp;
   cudaError_t e = grow(&h->outbuf, &h->out_cap, static_cast<size_t>(nb) * 16);

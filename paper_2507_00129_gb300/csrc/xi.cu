@@ -35,11 +35,12 @@
 namespace lya {
 namespace {
 
-constexpr int kHcap = 448;       // words per chunk-histogram array per warp: bins (K+1) x (n_par+1)
+constexpr int kHcap = 440;       // words per chunk-histogram array per warp: bins (K+1) x (n_par+1)
                                  // below kHcap - 32, then one dummy word per lane
 constexpr uint32_t kM15Bits = 0x4B400000u;   // bits of 1.5 * 2^23
 constexpr float kM15 = 12582912.0f;
-constexpr int kAcap = 384;       // accumulator entries per warp: rows x n_par
+constexpr int kAcap = 352;       // accumulator entries per warp: rows x n_par (7 rows of 50 bins;
+                                 // sized with kHcap so that 14 warps fit in shared memory)
 constexpr int kHcap64 = 256;     // doubles per histogram array per warp (FP64)
 constexpr int kMaxSeg = 1024;    // pixel buffer cap per warp
 

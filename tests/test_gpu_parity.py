@@ -353,6 +353,11 @@ def test_input_errors_are_reported(api, handle, c0):
     with pytest.raises(LyaError) as e:
         api.lya_xi(handle, api.DeviceCatalog.from_host(sub), synth.Bins(1000, 4, 10.0, 10.0))
     assert e.value.code == -8
+    # within the C-ABI grid limits but beyond the pair kernels' shared-memory layout
+    for prec, n_par in (("mixed", 204), ("fp64", 257)):
+        with pytest.raises(LyaError) as e:
+            api.lya_xi(handle, api.DeviceCatalog.from_host(sub), synth.Bins(n_par, 4, 10.0, 10.0), prec)
+        assert e.value.code == -8
     dc = api.DeviceCatalog.from_host(sub)
     api.lya_xi_pairs(handle, dc, bins, torch.tensor([0, 3, 25], dtype=torch.int32).cuda(),
                      torch.tensor([0, 5, 1], dtype=torch.int32).cuda())
