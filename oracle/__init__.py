@@ -16,8 +16,9 @@ Contents (each function cites the passage it follows):
 * ``subsample`` -- the seeded forest-pair subsample used for D    (Section 2.2)
 * ``adjoint``   -- gradient of L = sum_A c_A xi_A w.r.t. delta and w (chain rule of Eq. 2.4)
 * ``covariance``-- HEALPix sub-samples and the weighted sub-sample covariance of xi
+* ``xi3``       -- the anisotropic three-point estimator, Eq. (2.8), on the 5-variable triangle grid
 
 Everything is float64.  Readings of passages the paper leaves open are listed
 in the module docstrings.
 """
-from . import geometry, pairs, xi, project, dmat, subsample, adjoint, covariance  # noqa: F401
+from . import geometry, pairs, xi, project, dmat, subsample, adjoint, covariance, xi3  # noqa: F401
