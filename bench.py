@@ -663,6 +663,63 @@ def run_mocks(args, rank, world, local):
     h.close()
 
 
+def run_xi3(args, rank, world, local):
+    """The anisotropic three-point estimator on the SDSS-DR16-like catalogue:
+    r_max = 40 Mpc/h (the paper's 3PCF timings) with 4 Mpc/h radial bins,
+    10 theta bins and 20 cos(alpha) bins (the figure's bin widths)."""
+    import torch
+    from paper_2507_00129_gb300 import synth, build
+    build.build()
+    from paper_2507_00129_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = synth.spec_for(1, seed=rank_seed(rank))
+    if args.forests:
+        spec.area_deg2 = spec.area_deg2 * args.forests / spec.n_forests
+        spec.n_forests = args.forests
+    cat = synth.generate(spec, name="sdss_like")
+    grid = type("Grid3", (), {"n_r": 10, "n_theta": 10, "n_alpha": 20, "r_max": 40.0})
+    dc = api.DeviceCatalog.from_host(cat, device=dev)
+    h = api.Handle()
+    # records per bin with unit weights (untimed): the work count
+    _, cnt, _ = api.lya_xi3(h, dc.with_(weight=torch.ones_like(dc.weight)), grid)
+    api.lya_sync_status(h)
+    records = float(cnt.sum())
+    for _ in range(args.warmup):
+        api.lya_xi3(h, dc, grid)
+    torch.cuda.synchronize()
+    barrier(world)
+    ks = []
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = api.lya_kernel_launches()
+        e0.record()
+        for _ in range(args.steps):
+            api.lya_xi3(h, dc, grid)
+            ks.append(api.lya_stage_ms(h, "xi"))
+        e1.record()
+        torch.cuda.synchronize()
+        launches = api.lya_kernel_launches() - launches0
+    api.lya_sync_status(h)
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms, rec_total, value = aggregate(ms_local, records, world)
+    line = {
+        "metric": "triangle records/s (3PCF)", "value": value, "unit": "records/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "sdss_dr16_like_60k_xi3", "forests": spec.n_forests, "r_max": 40.0, "n_r": 10,
+                   "n_theta": 10, "n_alpha": 20, "bins": 200000,
+                   "unit": "records = (main vertex, ordered pair of two other pixels) with |r1|, |r2| < r_max"},
+        "records": records, "kernel_ms": float(np.median(ks)),
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,9 +730,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--forests", type=int, default=0,
                     help="profiling: use this many forests (same sky density) instead of the workload's")
-    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks"],
+    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks", "xi3"],
                     help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi; "
-                         "mocks: batch of 15,000-forest mocks, xi/W + D (2%%) in one launch each")
+                         "mocks: batch of 15,000-forest mocks, xi/W + D (2%%) in one launch each; "
+                         "xi3: three-point estimator on the 60,000-forest catalogue")
     ap.add_argument("--mocks", type=int, default=128, help="mocks per rank for --workload mocks")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
     args = ap.parse_args()
@@ -686,6 +744,8 @@ def main():
         run_desi(args, rank, world, local)
     elif args.workload == "mocks":
         run_mocks(args, rank, world, local)
+    elif args.workload == "xi3":
+        run_xi3(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

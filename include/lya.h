@@ -237,6 +237,36 @@ int lya_xi_subsamples(lya_handle* h, const lya_catalog* cat, const lya_bins* bin
 int lya_xi_covariance(lya_handle* h, const double* num_sub, const double* wsum_sub, int32_t n_sub,
                       int32_t n_bins, double* cov, double* xi, void* stream);
 
+/* Grid of the anisotropic three-point estimator (Section 2.3): n_r bins of
+ * the side lengths over [0, r_max), n_theta bins of the angles of the sides
+ * to the line of sight over [0, pi], n_alpha bins of the cosine of the inner
+ * angle over [-1, 1].  The paper's figure uses r_max = 80 Mpc/h with
+ * n_r = 20, n_theta = 10, n_alpha = 20. */
+typedef struct {
+  int32_t n_r;
+  int32_t n_theta;
+  int32_t n_alpha;
+  double r_max;
+} lya_bins3;
+
+/* Three-point estimator, Eq. (2.8):
+ *   xi3_A = sum_A (w d)_i (w d)_j (w d)_k / sum_A w_i w_j w_k
+ * over pixel triplets of three distinct forests.  A record is a main vertex
+ * i with r1 = x_j - x_i, r2 = x_k - x_i (x = d n); every pixel of a triplet is
+ * the main vertex once and the other two take (r1, r2) in both orders; a
+ * record needs |r1|, |r2| < r_max; theta is measured from the main vertex's
+ * line of sight.  Triangle index
+ *   A = (((i_r1 n_r + i_r2) n_alpha + i_alpha) n_theta + i_theta1) n_theta + i_theta2.
+ * num, wsum (required), xi (optional): [n_r^2 n_alpha n_theta^2] float64.
+ * The |r| and theta bins are computed in FP64, cos alpha in FP32; products
+ * in FP32 are added to FP64 bin sums.  Builds (and caches) the forest-pair
+ * list for r_par_max = r_perp_max = r_max.  A main vertex with more
+ * neighbours within r_max than the kernel holds (about 2,000 on GB300) is
+ * reported as LYA_ERR_TOO_LARGE by the next synchronising call.  Limits:
+ * n_r, n_theta <= 256, n_alpha <= 1024, at most 2^28 bins. */
+int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double* num, double* wsum,
+            double* xi, void* stream);
+
 /* Tally of the mixed path's bin-edge flips (Section 2.1 binning done with FP32
  * separations): over the forest pairs kept by the subsample rule of lya_dmat
  * (p_subsample >= 1 keeps all), every pixel pair is binned with the mixed

@@ -39,9 +39,14 @@ class LyaBins(ctypes.Structure):
                 ("r_perp_max", c_double)]
 
 
+class LyaBins3(ctypes.Structure):
+    _fields_ = [("n_r", c_int32), ("n_theta", c_int32), ("n_alpha", c_int32), ("r_max", c_double)]
+
+
 H = c_void_p
 CAT = POINTER(LyaCatalog)
 BINS = POINTER(LyaBins)
+BINS3 = POINTER(LyaBins3)
 
 # name -> (restype, argtypes), one entry per declaration of include/lya.h
 SIGNATURES = {
@@ -69,6 +74,7 @@ SIGNATURES = {
                                POINTER(c_double), c_void_p]),
     "lya_xi_subsamples": (c_int, [H, CAT, BINS, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xi_covariance": (c_int, [H, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "lya_xi3": (c_int, [H, CAT, BINS3, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_flip_tally": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
                                POINTER(c_double), POINTER(c_double), c_void_p]),
     "lya_stage_ms": (c_int, [H, c_int32, POINTER(ctypes.c_float)]),

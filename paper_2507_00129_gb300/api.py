@@ -289,6 +289,20 @@ def lya_xi_covariance(handle: Handle, num_sub: torch.Tensor, wsum_sub: torch.Ten
     return cov, xi
 
 
+def lya_xi3(handle: Handle, cat: DeviceCatalog, grid, stream=None):
+    """Three-point estimator on grid (n_r, n_theta, n_alpha, r_max): num, wsum, xi
+    as flat [n_r^2 n_alpha n_theta^2] tensors."""
+    nbins = grid.n_r * grid.n_r * grid.n_alpha * grid.n_theta * grid.n_theta
+    num = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    wsum = torch.empty_like(num)
+    xi = torch.empty_like(num)
+    c = cat.c()
+    b = _lib.LyaBins3(int(grid.n_r), int(grid.n_theta), int(grid.n_alpha), float(grid.r_max))
+    check(handle.h, _lib.load().lya_xi3(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(num), _ptr(wsum), _ptr(xi),
+                                        _stream(stream)))
+    return num, wsum, xi
+
+
 def lya_flip_tally(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float = 1.0, seed: int = 0,
                    stream=None):
     n, f = ctypes.c_int64(), ctypes.c_int64()

@@ -249,6 +249,7 @@ int flags_to_status(lya_handle* h, unsigned f) {
   int code = LYA_ERR_DEVICE_CHECK;
   if (f & FLAG_OFFSETS) { m += " inconsistent offsets or pair indices;"; code = LYA_ERR_DEVICE_CHECK; }
   if (f & FLAG_TOO_LONG) { m += " forest longer than 2^20 pixels;"; code = LYA_ERR_TOO_LARGE; }
+  if (f & FLAG_X3_CAP) { m += " a 3PCF main vertex has more neighbours within r_max than the kernel holds;"; code = LYA_ERR_TOO_LARGE; }
   if (f & FLAG_NEGATIVE_W) { m += " negative weight;"; code = LYA_ERR_NONFINITE; }
   if (f & FLAG_NONFINITE) { m += " non-finite or non-positive value;"; code = LYA_ERR_NONFINITE; }
   if (f & FLAG_UNSORTED) { m += " distances not strictly increasing within a forest;"; code = LYA_ERR_UNSORTED; }
@@ -962,6 +963,45 @@ int lya_xi_covariance(lya_handle* h, const double* num_sub, const double* wsum_s
   cudaError_t e = grow(&h->outbuf, &h->out_cap, covariance_scratch_bytes(n_sub, n_bins));
   if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "covariance scratch");
   CK(launch_covariance(num_sub, wsum_sub, n_sub, n_bins, cov, xi, h->outbuf, s), "covariance");
+  return LYA_OK;
+}
+
+int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double* num, double* wsum, double* xi,
+            void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (!bins) return fail(h, LYA_ERR_INVALID_ARG, "bins is NULL");
+  if (bins->n_r < 1 || bins->n_r > 256 || bins->n_theta < 1 || bins->n_theta > 256 || bins->n_alpha < 1 ||
+      bins->n_alpha > 1024)
+    return fail(h, LYA_ERR_TOO_LARGE, "3PCF grid outside n_r, n_theta <= 256, n_alpha <= 1024");
+  const int64_t nbins = static_cast<int64_t>(bins->n_r) * bins->n_r * bins->n_alpha * bins->n_theta * bins->n_theta;
+  if (nbins > (1LL << 28)) return fail(h, LYA_ERR_TOO_LARGE, "3PCF grid above 2^28 bins");
+  if (!(bins->r_max > 0) || !std::isfinite(bins->r_max)) return fail(h, LYA_ERR_INVALID_ARG, "r_max must be > 0");
+  if (!num || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "num and wsum are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (int st0 = check_capture_stream(h, s)) return st0;
+  int st = prepare(h, cat, 1, s);
+  if (st) return st;
+  // forest pairs that can hold two pixels closer than r_max: the 2PCF list for r_par_max = r_perp_max = r_max
+  const lya_bins nb2{1, 1, bins->r_max, bins->r_max};
+  st = ensure_pairs(h, cat, 1, &nb2, s);
+  if (st) return st;
+  X3Args A;
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.dist = cat->dist;
+  A.n_pix = cat->n_pix;
+  A.n_r = bins->n_r;
+  A.n_theta = bins->n_theta;
+  A.n_alpha = bins->n_alpha;
+  A.r_max = bins->r_max;
+  A.num = num;
+  A.wsum = wsum;
+  A.xi = xi;
+  stage_begin(h, 0, s);
+  CK(run_xi3(A, h->dev, &h->scratch2, &h->scratch2_cap, h->d_err, s), "xi3");
+  stage_end(h, 0, s);
   return LYA_OK;
 }
 

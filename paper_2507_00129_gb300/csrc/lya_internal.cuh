@@ -15,6 +15,7 @@ enum : unsigned {
   FLAG_OFFSETS = 4u,
   FLAG_NEGATIVE_W = 8u,
   FLAG_TOO_LONG = 16u,
+  FLAG_X3_CAP = 32u,      // a 3PCF main vertex had more neighbours than the kernel's capacity
 };
 
 // Per-forest data derived by the preparation kernel (structure of arrays).
@@ -225,6 +226,23 @@ struct AdjArgs {
 };
 cudaError_t run_adjoint(const AdjArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
                         cudaStream_t s);
+
+// xi3.cu: three-point estimator, Eq. (2.8)
+struct X3Args {
+  const int2* pairs;     // forest pairs (a < b) that can hold pixels within r_max
+  int64_t n_pairs;
+  const Pix* pix;
+  Forests F;
+  const double* dist;    // caller's FP64 distances (single catalogue: packed index = pixel index)
+  int64_t n_pix;
+  int n_r, n_theta, n_alpha;
+  double r_max;
+  double* num;           // [n_r^2 n_alpha n_theta^2]
+  double* wsum;
+  double* xi;            // optional
+};
+cudaError_t run_xi3(const X3Args& a, const DevInfo& dev, void** scratch, size_t* scratch_cap, unsigned* err,
+                    cudaStream_t s);
 
 // scratch helper (api.cu).  While the calling thread captures a CUDA graph
 // (lya_capture_begin) it allocates nothing and fails with
