@@ -260,10 +260,12 @@ typedef struct {
  * num, wsum (required), xi (optional): [n_r^2 n_alpha n_theta^2] float64.
  * The |r| and theta bins are computed in FP64, cos alpha in FP32; products
  * in FP32 are added to FP64 bin sums.  Builds (and caches) the forest-pair
- * list for r_par_max = r_perp_max = r_max.  A main vertex with more
- * neighbours within r_max than the kernel holds (about 2,000 on GB300) is
- * reported as LYA_ERR_TOO_LARGE by the next synchronising call.  Limits:
- * n_r, n_theta <= 256, n_alpha <= 1024, at most 2^28 bins. */
+ * list for r_par_max = r_perp_max = r_max.  Synchronises (a counting pass
+ * sizes the kernel's neighbour capacity to the largest list); not allowed
+ * during graph capture.  A main vertex with more neighbours within r_max
+ * than one block holds (about 6,400 on GB300) is reported as
+ * LYA_ERR_TOO_LARGE by the next synchronising call.  Limits: n_r, n_theta
+ * <= 256, n_alpha <= 1024, at most 2^28 bins. */
 int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double* num, double* wsum,
             double* xi, void* stream);
 
@@ -343,8 +345,8 @@ int64_t lya_kernel_launches(void);
  *    LYA_ERR_INVALID_ARG (again: run the same calls once before capturing);
  *  - fail with LYA_ERR_INVALID_ARG if they would synchronise (lya_sync_status,
  *    lya_pairs_build, lya_pairs_get, lya_xi_pairs, lya_autotune,
- *    lya_pair_stats, lya_flip_tally, lya_stage_ms, lya_last_launch) or use
- *    another stream.
+ *    lya_pair_stats, lya_flip_tally, lya_xi3, lya_stage_ms, lya_last_launch)
+ *    or use another stream.
  * Input checks still run on the device at every replay; read them with
  * lya_sync_status after a replay.  Outputs (caller pointers and the handle's
  * scratch) are fixed at capture.

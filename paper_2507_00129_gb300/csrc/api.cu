@@ -977,8 +977,8 @@ int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double
   if (nbins > (1LL << 28)) return fail(h, LYA_ERR_TOO_LARGE, "3PCF grid above 2^28 bins");
   if (!(bins->r_max > 0) || !std::isfinite(bins->r_max)) return fail(h, LYA_ERR_INVALID_ARG, "r_max must be > 0");
   if (!num || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "num and wsum are required");
+  if (int st0 = refuse_in_capture(h, "lya_xi3")) return st0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (int st0 = check_capture_stream(h, s)) return st0;
   int st = prepare(h, cat, 1, s);
   if (st) return st;
   // forest pairs that can hold two pixels closer than r_max: the 2PCF list for r_par_max = r_perp_max = r_max

@@ -19,9 +19,10 @@
 //     of side 1 is not above side 2's, with weight 2 when both keys are equal;
 //     sums are FP32 products added to FP64 bin sums with global atomics;
 //  3. a finalize kernel copies each canonical bin to its mirror and forms xi.
-// A vertex with more neighbours than the shared-memory capacity raises a
-// device flag (reported as LYA_ERR_TOO_LARGE) instead of being truncated
-// silently.
+// A counting pass first finds the largest neighbour list, and the block's
+// shared-memory capacity is sized to it (fewer blocks per SM when lists are
+// long); a vertex beyond what one block can hold raises a device flag
+// (reported as LYA_ERR_TOO_LARGE) instead of being truncated silently.
 #include <algorithm>
 #include <math.h>
 
@@ -193,6 +194,47 @@ __global__ void __launch_bounds__(kX3Threads) xi3_kernel(X3Args A, const int32_t
   }
 }
 
+// largest number of neighbours within r_max of any main vertex (the same
+// exact FP64 test as the gather of xi3_kernel), one warp per vertex pixel
+__global__ void xi3_count_kernel(X3Args A, const int32_t* nbr, const int64_t* nstart, int* max_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double rmax2 = A.r_max * A.r_max;
+  int best = 0;
+  for (int64_t g = warp; g < A.n_pix; g += nw) {
+    const int f = forest_of(A.F, g);
+    if (g - A.F.off[f] >= A.F.len[f]) continue;
+    const double nax = A.F.ux[f], nay = A.F.uy[f], naz = A.F.uz[f];
+    const double di = A.dist[g];
+    const double xi = di * nax, yi = di * nay, zi = di * naz;
+    int cnt = 0;
+    for (int64_t e = nstart[f]; e < nstart[f + 1]; ++e) {
+      const int o = nbr[e];
+      const int no = A.F.len[o];
+      if (no == 0) continue;
+      const double c = nax * A.F.ux[o] + nay * A.F.uy[o] + naz * A.F.uz[o];
+      const double disc = rmax2 - di * di * fmax(0.0, 1.0 - c * c);
+      if (!(disc > 0.0)) continue;
+      const double sq = sqrt(disc);
+      const Pix* po = A.pix + A.F.off[o];
+      const double ref = A.F.dref[o];
+      const float lo = static_cast<float>(di * c - sq - ref) - 1e-2f;
+      const float hi = static_cast<float>(di * c + sq - ref) + 1e-2f;
+      const int jlo = count_below(po, no, lo), jhi = count_below(po, no, hi);
+      for (int j = jlo + lane; j < jhi; j += 32) {
+        const double dj = A.dist[A.F.off[o] + j];
+        const double dx = dj * A.F.ux[o] - xi, dy = dj * A.F.uy[o] - yi, dz = dj * A.F.uz[o] - zi;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        cnt += (r2 < rmax2 && r2 > 0.0) ? 1 : 0;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    best = max(best, cnt);
+  }
+  if (lane == 0 && best > 0) atomicMax(max_count, best);
+}
+
 // copy each canonical bin (side-1 key <= side-2 key) to its mirror; xi = N / W
 __global__ void xi3_finalize_kernel(double* num, double* wsum, double* xi, int nr, int nt, int na) {
   const int64_t n = static_cast<int64_t>(nr) * nr * na * nt * nt;
@@ -260,9 +302,19 @@ cudaError_t run_xi3(const X3Args& a, const DevInfo& dev, void** scratch, size_t*
   LYA_COUNT(1), x3_scan_kernel<<<1, 1024, 0, s>>>(deg, nf, start);
   if (np > 0) LYA_COUNT(1), x3_fill_kernel<<<grid_for(np, 256), 256, 0, s>>>(a.pairs, np, start, cur, nbr);
   LYA_TRY(cudaGetLastError());
-  // neighbour capacity per block: as much shared memory as leaves three blocks per SM
+  // neighbour capacity per block: the largest neighbour list of any vertex
+  // (counting pass, synchronising), at least what leaves three blocks per SM;
+  // a list beyond one block's shared memory is reported, not truncated
   const int per_cand = 9 * 4;
-  int cap = std::min(4096, (dev.smem_per_sm / 3 - 2048) / per_cand);
+  int* dmax = reinterpret_cast<int*>(sc + o_misc + 64);
+  LYA_TRY(cudaMemsetAsync(dmax, 0, 4, s));
+  if (a.n_pix > 0 && nf > 0)
+    LYA_COUNT(1), xi3_count_kernel<<<dev.sms * 8, 256, 0, s>>>(a, nbr, start, dmax);
+  int hmax = 0;
+  LYA_TRY(cudaMemcpyAsync(&hmax, dmax, 4, cudaMemcpyDeviceToHost, s));
+  LYA_TRY(cudaStreamSynchronize(s));
+  const int cap_max = (dev.smem_optin - 1024) / per_cand;
+  int cap = std::max(std::min(cap_max, (dev.smem_per_sm / 3 - 2048) / per_cand), std::min(hmax, cap_max));
   cap = std::max(cap, 256);
   const int smem = cap * per_cand;
   if (smem > dev.smem_optin) return cudaErrorInvalidValue;

@@ -77,3 +77,34 @@ def test_xi3_argument_errors(api, handle):
     with pytest.raises(LyaError) as e:
         api.lya_xi3(handle, dc, ox3.Grid3(n_r=5, n_theta=10, n_alpha=20, r_max=-1.0))
     assert e.value.code == -1
+
+
+def test_xi3_dense_forests_use_a_larger_capacity(api, handle):
+    """DESI-like pixel density (0.57 Mpc/h spacing) at r_max = 40 Mpc/h puts
+    thousands of pixels around a vertex; the call sizes its capacity to the
+    largest list and counts every record: with unit weights the total weight
+    equals, summed over vertices, (sum_f c_f)^2 - sum_f c_f^2, c_f the vertex's
+    in-range pixels of forest f (ordered pairs from distinct forests)."""
+    spec = synth.Spec(n_forests=80, seed=12, region="box", box_deg=0.8, grid="linear", delta_sigma=0.25,
+                      length_range=(300, 600))
+    cat = synth.generate(spec)
+    cat.weight[:] = 1.0
+    g = ox3.Grid3(n_r=10, n_theta=10, n_alpha=20, r_max=40.0)
+    _, wsum, _ = api.lya_xi3(handle, api.DeviceCatalog.from_host(cat), g)
+    api.lya_sync_status(handle)
+    from oracle.geometry import unit_vectors
+    n = unit_vectors(cat.ra, cat.dec)
+    forest = np.repeat(np.arange(cat.n_forests), np.diff(cat.offsets))
+    pos = cat.dist[:, None] * n[forest]
+    total, most = 0.0, 0
+    for i in range(cat.n_pix):
+        d2 = np.einsum("ij,ij->i", pos - pos[i], pos - pos[i])
+        m = (forest != forest[i]) & (d2 < 40.0 ** 2)
+        c = np.bincount(forest[m], minlength=cat.n_forests).astype(np.float64)
+        total += c.sum() ** 2 - (c * c).sum()
+        most = max(most, int(m.sum()))
+    assert most > 2200          # beyond three blocks' shared memory per SM
+    W = _np(wsum)
+    assert abs(W.sum() - total) <= 1e-9 * total + 10
+    Wr = W.reshape(g.n_r, g.n_r, g.n_alpha, g.n_theta, g.n_theta)
+    np.testing.assert_array_equal(Wr, Wr.transpose(1, 0, 2, 4, 3))
