@@ -13,8 +13,9 @@
 //     pixels within r_max of the vertex (a contiguous range of the sorted
 //     distances, cut by binary search, then tested exactly) go to shared
 //     memory with r in FP32 and their |r| and theta bins computed in FP64;
-//  2. pairs: each warp takes rows p, its lanes the columns q > p; pixels of
-//     the same forest are skipped; cos alpha is FP32; the record and its
+//  2. pairs: each warp holds 32 candidates q in registers and walks the
+//     candidates p < q (one shared-memory read per p for the whole warp);
+//     pixels of the same forest are skipped; cos alpha is FP32; the record and its
 //     mirror (sides swapped) are added once, to the bin whose (r, theta) key
 //     of side 1 is not above side 2's, with weight 2 when both keys are equal;
 //     sums are FP32 products added to FP64 bin sums with global atomics;
@@ -93,15 +94,9 @@ __device__ __forceinline__ int forest_of(const Forests& F, int64_t g) {
 __global__ void __launch_bounds__(kX3Threads) xi3_kernel(X3Args A, const int32_t* nbr, const int64_t* nstart,
                                                          int cap, unsigned long long* counter, unsigned* err) {
   extern __shared__ __align__(16) unsigned char sm[];
-  float* rx = reinterpret_cast<float*>(sm);
-  float* ry = rx + cap;
-  float* rz = ry + cap;
-  float* ir_ = rz + cap;         // 1 / |r|
-  float* wd = ir_ + cap;
-  float* ww = wd + cap;
-  int32_t* kr = reinterpret_cast<int32_t*>(ww + cap);   // radial bin
-  int32_t* kt = kr + cap;                               // theta bin
-  int32_t* kf = kt + cap;                               // forest
+  float4* cr = reinterpret_cast<float4*>(sm);                  // r (FP32) and 1 / |r|
+  float2* cw = reinterpret_cast<float2*>(cr + cap);            // (w d, w)
+  int2* ck = reinterpret_cast<int2*>(cw + cap);                // ((radial bin << 16) | theta bin, forest)
   __shared__ int s_n;
   __shared__ long long s_item;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarps = blockDim.x >> 5;
@@ -154,39 +149,42 @@ __global__ void __launch_bounds__(kX3Threads) xi3_kernel(X3Args A, const int32_t
         const int ir = min(static_cast<int>(r * inv_dr), nr - 1);
         const int it = min(static_cast<int>(acos(fmin(1.0, fmax(-1.0, ct))) * inv_dt), nt - 1);
         const Pix q = po[j];
-        rx[slot] = static_cast<float>(dx);
-        ry[slot] = static_cast<float>(dy);
-        rz[slot] = static_cast<float>(dz);
-        ir_[slot] = static_cast<float>(1.0 / r);
-        wd[slot] = q.z;
-        ww[slot] = q.y;
-        kr[slot] = ir;
-        kt[slot] = it;
-        kf[slot] = o;
+        cr[slot] = make_float4(static_cast<float>(dx), static_cast<float>(dy), static_cast<float>(dz),
+                               static_cast<float>(1.0 / r));
+        cw[slot] = make_float2(q.z, q.y);
+        ck[slot] = make_int2((ir << 16) | it, o);
       }
     }
     __syncthreads();
     const int P = s_n;
     if (P > cap && tid == 0) atomicOr(err, FLAG_X3_CAP);
-    // 2. unordered pairs (p < q) of neighbours from two distinct forests
+    // 2. unordered pairs (p < q) of neighbours from two distinct forests: a
+    //    warp holds a tile of 32 candidates q in registers (one per lane) and
+    //    walks the candidates p below them, each read once for the whole warp
     if (P <= cap) {
-      for (int p = wid; p < P; p += nwarps) {
-        const float px = rx[p], py = ry[p], pz = rz[p], pi = ir_[p];
-        const float pwd = wd[p] * wd_i, pw = ww[p] * w_i;
-        const int pr = kr[p], pt = kt[p], pf = kf[p];
-        const int pkey = pr * nt + pt;
-        for (int q = p + 1 + lane; q < P; q += 32) {
-          if (kf[q] == pf) continue;
-          const float ca = (px * rx[q] + py * ry[q] + pz * rz[q]) * (pi * ir_[q]);
+      for (int q0 = wid * 32; q0 < P; q0 += nwarps * 32) {
+        const int q = q0 + lane;
+        const bool qv = q < P;
+        const float4 rq = qv ? cr[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 wq = qv ? cw[q] : make_float2(0.f, 0.f);
+        const int2 kq = qv ? ck[q] : make_int2(0, -1);
+        const float wdq = wq.x * wd_i, wwq = wq.y * w_i;
+        const int qr = kq.x >> 16, qt = kq.x & 0xffff;
+        const int pend = min(q0 + 32, P);
+        for (int p = 0; p < pend; ++p) {
+          const float4 rp = cr[p];
+          const int2 kp = ck[p];
+          if (!qv || p >= q || kp.y == kq.y) continue;
+          const float2 wp = cw[p];
+          const float ca = (rp.x * rq.x + rp.y * rq.y + rp.z * rq.z) * (rp.w * rq.w);
           const int ia = min(max(static_cast<int>(floorf((ca + 1.0f) * half_na)), 0), na - 1);
-          const int qr = kr[q], qt = kt[q];
-          const int qkey = qr * nt + qt;
+          const int pr = kp.x >> 16, pt = kp.x & 0xffff;
           int r1, t1, r2, t2;
-          if (pkey <= qkey) { r1 = pr; t1 = pt; r2 = qr; t2 = qt; } else { r1 = qr; t1 = qt; r2 = pr; t2 = pt; }
-          const float mult = (pkey == qkey) ? 2.f : 1.f;
+          if (kp.x <= kq.x) { r1 = pr; t1 = pt; r2 = qr; t2 = qt; } else { r1 = qr; t1 = qt; r2 = pr; t2 = pt; }
+          const float mult = (kp.x == kq.x) ? 2.f : 1.f;
           const int64_t bin = (((static_cast<int64_t>(r1) * nr + r2) * na + ia) * nt + t1) * nt + t2;
-          red_add_f64_global(A.num + bin, static_cast<double>(pwd * wd[q] * mult));
-          red_add_f64_global(A.wsum + bin, static_cast<double>(pw * ww[q] * mult));
+          red_add_f64_global(A.num + bin, static_cast<double>(wp.x * wdq * mult));
+          red_add_f64_global(A.wsum + bin, static_cast<double>(wp.y * wwq * mult));
         }
       }
     }
@@ -305,7 +303,7 @@ cudaError_t run_xi3(const X3Args& a, const DevInfo& dev, void** scratch, size_t*
   // neighbour capacity per block: the largest neighbour list of any vertex
   // (counting pass, synchronising), at least what leaves three blocks per SM;
   // a list beyond one block's shared memory is reported, not truncated
-  const int per_cand = 9 * 4;
+  const int per_cand = 32;
   int* dmax = reinterpret_cast<int*>(sc + o_misc + 64);
   LYA_TRY(cudaMemsetAsync(dmax, 0, 4, s));
   if (a.n_pix > 0 && nf > 0)
