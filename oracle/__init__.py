@@ -17,8 +17,10 @@ Contents (each function cites the passage it follows):
 * ``adjoint``   -- gradient of L = sum_A c_A xi_A w.r.t. delta and w (chain rule of Eq. 2.4)
 * ``covariance``-- HEALPix sub-samples and the weighted sub-sample covariance of xi
 * ``xi3``       -- the anisotropic three-point estimator, Eq. (2.8), on the 5-variable triangle grid
+* ``xcf``       -- forest x quasar cross-correlation and its distortion matrix (readings of Eq. 2.4-2.7)
+* ``xi1d``      -- the same-forest (1D) correlation that Eq. (2.4) excludes
 
 Everything is float64.  Readings of passages the paper leaves open are listed
 in the module docstrings.
 """
-from . import geometry, pairs, xi, project, dmat, subsample, adjoint, covariance, xi3  # noqa: F401
+from . import geometry, pairs, xi, project, dmat, subsample, adjoint, covariance, xi3, xcf, xi1d  # noqa: F401

@@ -73,6 +73,7 @@ class Catalog:
     delta: np.ndarray     # [n_pix] float32
     weight: np.ndarray    # [n_pix] float32
     name: str = ""
+    zq: Optional[np.ndarray] = None   # [n_forests] float64, redshift of each forest's quasar
 
     @property
     def n_forests(self) -> int:
@@ -215,7 +216,54 @@ def generate(spec: Spec, name: str = "") -> Catalog:
         lam_c = np.log(0.5 * (RF_MIN + RF_MAX) * (1.0 + zq))
         delta = delta + a[forest_of_pix] + bslope[forest_of_pix] * (loglam - lam_c[forest_of_pix])
     return Catalog(ra=ra, dec=dec, offsets=offsets, dist=dist, loglam=loglam,
-                   delta=delta.astype(np.float32), weight=weight, name=name)
+                   delta=delta.astype(np.float32), weight=weight, name=name, zq=zq)
+
+
+@dataclasses.dataclass
+class Quasars:
+    """Point tracers for the forest x quasar cross-correlation."""
+
+    ra: np.ndarray        # [n] float64, radians
+    dec: np.ndarray       # [n] float64, radians
+    dist: np.ndarray      # [n] float64, comoving distance, Mpc/h
+    weight: np.ndarray    # [n] float32
+    z: np.ndarray         # [n] float64
+
+    @property
+    def n(self) -> int:
+        return int(self.ra.shape[0])
+
+
+def quasars(spec: Spec, cat: Catalog, extra_fraction: float = 0.5, z_extra=(1.8, 3.5)):
+    """Quasar catalogue of a forest catalogue drawn from ``spec``.
+
+    Quasar a (a < n_forests) is the source of forest a: its line of sight and
+    redshift z_q.  ``round(extra_fraction * n_forests)`` further quasars
+    without a forest follow, drawn from ``default_rng([spec.seed, 7])`` in this
+    order: positions uniform in area over the same region, then
+    z ~ U[z_extra].  Weights w_q = ((1 + z) / 3.25)^0.44, the redshift
+    evolution of the quasar weights of the eBOSS DR16 analysis
+    (du Mas des Bourboux et al. 2020).  Returns (quasars, forest_qso) with
+    forest_qso[a] = a, the index of each forest's own quasar."""
+    if cat.zq is None:
+        raise ValueError("catalogue has no quasar redshifts")
+    n = cat.n_forests
+    n_extra = int(round(extra_fraction * n))
+    rng = np.random.default_rng([spec.seed, 7])
+    if spec.region == "box":
+        b = math.radians(spec.box_deg)
+        ra_x = rng.uniform(0.0, b, n_extra)
+        sd_x = rng.uniform(math.sin(-0.5 * b), math.sin(0.5 * b), n_extra)
+    else:
+        th = math.radians(cap_half_angle_deg(spec.area_deg2))
+        ra_x = rng.uniform(0.0, 2.0 * math.pi, n_extra)
+        sd_x = rng.uniform(math.cos(th), 1.0, n_extra)
+    z_x = rng.uniform(z_extra[0], z_extra[1], n_extra)
+    z = np.concatenate([np.asarray(cat.zq, dtype=np.float64), z_x])
+    q = Quasars(ra=np.concatenate([cat.ra, ra_x]), dec=np.concatenate([cat.dec, np.arcsin(sd_x)]),
+                dist=comoving_distance(z, spec.omega_m),
+                weight=(((1.0 + z) / 3.25) ** 0.44).astype(np.float32), z=z)
+    return q, np.arange(n, dtype=np.int64)
 
 
 # ----------------------------------------------------------------------------
@@ -280,7 +328,8 @@ def concat(cats: Sequence[Catalog]) -> Catalog:
         offsets=np.concatenate(offs), dist=np.concatenate([c.dist for c in cats]),
         loglam=np.concatenate([c.loglam for c in cats]),
         delta=np.concatenate([c.delta for c in cats]), weight=np.concatenate([c.weight for c in cats]),
-        name="+".join(c.name for c in cats))
+        name="+".join(c.name for c in cats),
+        zq=np.concatenate([c.zq for c in cats]) if all(c.zq is not None for c in cats) else None)
 
 
 def subset(cat: Catalog, forests: np.ndarray) -> Catalog:
@@ -293,4 +342,4 @@ def subset(cat: Catalog, forests: np.ndarray) -> Catalog:
         if len(forests) else np.zeros(0, dtype=np.int64)
     return Catalog(ra=cat.ra[forests], dec=cat.dec[forests], offsets=offs, dist=cat.dist[idx],
                    loglam=cat.loglam[idx], delta=cat.delta[idx], weight=cat.weight[idx],
-                   name=cat.name + "[subset]")
+                   name=cat.name + "[subset]", zq=None if cat.zq is None else cat.zq[forests])
