@@ -720,6 +720,109 @@ def run_xi3(args, rank, world, local):
     h.close()
 
 
+def run_xcf(args, rank, world, local):
+    """Forest x quasar cross-correlation on the SDSS-DR16-like catalogue: 60,000
+    forests, 90,000 quasars (each forest's own plus 30,000 without a forest),
+    r_par in [-200, 200) Mpc/h in 100 bins, r_perp < 200 in 50.  A step is the
+    pair build, the cross-correlation and its distortion matrix (2% of the
+    forest-quasar pairs); the 1D same-forest correlation (50 bins to 200 Mpc/h)
+    is timed on its own."""
+    import time
+    import torch
+    from paper_2507_00129_gb300 import synth, build
+    build.build()
+    from paper_2507_00129_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = synth.spec_for(1, seed=rank_seed(rank))
+    if args.forests:
+        spec.area_deg2 = spec.area_deg2 * args.forests / spec.n_forests
+        spec.n_forests = args.forests
+    cat = synth.generate(spec, name="sdss_like")
+    qso, own = synth.quasars(spec, cat, extra_fraction=0.5)
+    bins = synth.Bins(100, 50, 200.0, 200.0)
+    p_dm, seed = 0.02, 2024
+    dc = api.DeviceCatalog.from_host(cat, device=dev)
+    dq = api.DeviceQuasars.from_host(qso, device=dev)
+    own_d = torch.from_numpy(own).to(dev)
+    h = api.Handle()
+    # work counts with unit weights (untimed)
+    ones_q = api.DeviceQuasars(dq.ra, dq.dec, dq.dist, torch.ones_like(dq.weight))
+    _, cnt, _ = api.lya_xcf(h, dc.with_(weight=torch.ones_like(dc.weight)), ones_q, bins, forest_qso=own_d)
+    n_xpairs = int(api.lya_last_launch(h)["pairs"])
+    _, cnt1, _ = api.lya_xi1d(h, dc.with_(weight=torch.ones_like(dc.weight)), 50, 200.0)
+    api.lya_sync_status(h)
+    pix_pairs, pix_pairs_1d = float(cnt.sum()), float(cnt1.sum())
+
+    def step():
+        api.lya_xcf(h, dc, dq, bins, forest_qso=own_d)
+        api.lya_xdmat(h, dc, dq, bins, p_dm, seed, forest_qso=own_d)
+
+    for _ in range(args.warmup):
+        step()
+        api.lya_xi1d(h, dc, 50, 200.0)
+    torch.cuda.synchronize()
+    barrier(world)
+    st = {"xcf": [], "xdmat": [], "pairs": []}
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = api.lya_kernel_launches()
+        e0.record()
+        for _ in range(args.steps):
+            api.lya_xcf(h, dc, dq, bins, forest_qso=own_d)
+            st["xcf"].append(api.lya_stage_ms(h, "xi"))
+            st["pairs"].append(api.lya_stage_ms(h, "pairs"))
+            api.lya_xdmat(h, dc, dq, bins, p_dm, seed, forest_qso=own_d)
+            st["xdmat"].append(api.lya_stage_ms(h, "dmat"))
+        e1.record()
+        torch.cuda.synchronize()
+        launches = api.lya_kernel_launches() - launches0
+        # 1D correlation, timed on its own
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(args.steps):
+            api.lya_xi1d(h, dc, 50, 200.0)
+        f1.record()
+        torch.cuda.synchronize()
+    api.lya_sync_status(h)
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms1d = f0.elapsed_time(f1) / args.steps
+    ms, tot, value = aggregate(ms_local, pix_pairs, world)
+    line = {
+        "metric": "forest-quasar pixel pairs/s (cross-correlation + its D)", "value": value,
+        "unit": "pixel-quasar pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "sdss_dr16_like_60k_xcf", "forests": spec.n_forests, "quasars": qso.n,
+                   "bins": [bins.n_par, bins.n_perp], "r_par": [-200.0, 200.0], "r_perp_max": 200.0,
+                   "dm_fraction": p_dm, "l2": "inputs 0.2 GB + 90k quasars; D~ 200 MB > L2",
+                   "unit": "in-grid (pixel, quasar) pairs"},
+        "pixel_quasar_pairs": pix_pairs, "forest_quasar_pairs": n_xpairs,
+        "stages_ms": {k: float(np.median(v)) for k, v in st.items()},
+        "xi1d": {"ms": ms1d, "pixel_pairs": pix_pairs_1d, "pairs_per_s": pix_pairs_1d / (ms1d * 1e-3),
+                 "bins": 50, "r_max": 200.0},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        nf = min(600, cat.n_forests)
+        sub = synth.subset(cat, np.arange(nf))
+        t0 = time.perf_counter()
+        pl = oracle.xcf.forest_quasar_pairs(sub, qso, bins, own[:nf])
+        ref = oracle.xcf.xcf_sums(sub, qso, bins, pl)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": float(ref["count"].sum()) / dt, "unit": "pixel-quasar pairs/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"cross-correlation sums of the first {nf} forests with all quasars "
+                                          f"({dt:.1f} s, pair search included; D not included)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -730,10 +833,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--forests", type=int, default=0,
                     help="profiling: use this many forests (same sky density) instead of the workload's")
-    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks", "xi3"],
+    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks", "xi3", "xcf"],
                     help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi; "
                          "mocks: batch of 15,000-forest mocks, xi/W + D (2%%) in one launch each; "
-                         "xi3: three-point estimator on the 60,000-forest catalogue")
+                         "xi3: three-point estimator on the 60,000-forest catalogue; "
+                         "xcf: forest x quasar cross-correlation, its D and the 1D correlation")
     ap.add_argument("--mocks", type=int, default=128, help="mocks per rank for --workload mocks")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
     args = ap.parse_args()
@@ -746,6 +850,8 @@ def main():
         run_mocks(args, rank, world, local)
     elif args.workload == "xi3":
         run_xi3(args, rank, world, local)
+    elif args.workload == "xcf":
+        run_xcf(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -269,6 +269,63 @@ typedef struct {
 int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double* num, double* wsum,
             double* xi, void* stream);
 
+/* Point tracers (quasars) for the forest x quasar cross-correlation.  Entries
+ * with a non-finite or non-positive distance, non-finite position or weight,
+ * or a negative weight are skipped and flagged (LYA_ERR_NONFINITE at the
+ * call's own check). */
+typedef struct {
+  int64_t n;
+  const double* ra;       /* [n] right ascension, radians */
+  const double* dec;      /* [n] declination, radians */
+  const double* dist;     /* [n] comoving distance, Mpc/h */
+  const float* weight;    /* [n] quasar weight w_q >= 0 */
+} lya_quasars;
+
+/* Forest x quasar cross-correlation (the extension of Section 4; Eq. (2.4)
+ * with the quasar as second point, weight w_q and no delta):
+ *   num[A] = sum_{(i,q) in A} (w delta)_i w_q,  wsum[A] = sum w_i w_q,  xi = num/wsum,
+ * r_par = (d_i - d_q) cos(theta/2) (signed), r_perp = (d_i + d_q) sin(theta/2),
+ * A = p*n_perp + t with p = floor((r_par + r_par_max) / D_par),
+ * D_par = 2 r_par_max / n_par (the grid spans [-r_par_max, r_par_max)), and
+ * t = floor(r_perp / D_perp), D_perp = r_perp_max / n_perp.
+ * Every pixel of every forest pairs with every quasar except the forest's own:
+ * forest_qso ([n_forests] device int64, may be NULL) gives the index of each
+ * forest's quasar in qso (-1 = none).  num, wsum required, xi optional, each
+ * [n_par*n_perp] float64.  FP32 separations (bin decisions within about
+ * 6e-5 bin widths of an edge may differ from FP64 ones), exact per-run sums,
+ * FP64 accumulation.  Builds the (forest, quasar) pair list each call
+ * (synchronises); refused during graph capture.  Limits: check of lya_bins,
+ * and 16 bytes per bin of shared memory (n_par*n_perp <= 14,000 or so on
+ * GB300; else LYA_ERR_TOO_LARGE). */
+int lya_xcf(lya_handle* h, const lya_catalog* cat, const lya_quasars* qso, const int64_t* forest_qso,
+            const lya_bins* bins, double* num, double* wsum, double* xi, void* stream);
+
+/* Distortion matrix of the cross-correlation (Eq. (2.6) with the projection
+ * eta of Eq. (2.7) acting on the forest only):
+ *   D_AB = W_A^-1 sum_{(a,q)} sum_{i: (i,q) in A} w_i w_q sum_{k: (k,q) in B} eta_ik,
+ * W_A (wsum_dm, [nb] float64, optional) the weight sum over the kept
+ * (forest, quasar) pairs: (a, q) is kept iff p_subsample >= 1 or
+ * SplitMix64(seed XOR (a*2^32 + q)) < floor(p_subsample * 2^64) (the rule of
+ * lya_dmat on the ordered pair).  dmat: [nb*nb] float64, row A, column B.
+ * Computed from eta = I - rank 2: the pair adds
+ * w_q (diag(alpha) - alpha alpha^T / W_a - beta beta^T / S_a) with the
+ * per-bin sums alpha = sum w_k, beta = sum w_k (Lambda_k - Lbar_a).
+ * Refused during graph capture.  Limits: nb^2 doubles of scratch; forests up
+ * to ~11,000 pixels (20 bytes of shared memory per pixel per warp). */
+int lya_xdmat(lya_handle* h, const lya_catalog* cat, const lya_quasars* qso, const int64_t* forest_qso,
+              const lya_bins* bins, lya_eta eta, double p_subsample, uint64_t seed, double* dmat,
+              double* wsum_dm, void* stream);
+
+/* Same-forest (one-dimensional) correlation: Eq. (2.4) over the pixel pairs
+ * i < j of one forest that the three-dimensional estimator excludes
+ * (Section 2.1), binned in p = floor(|d_i - d_j| / (r_max / n_bins)),
+ * p < n_bins.  num, wsum required, xi optional, each [n_bins] float64.
+ * FP64 throughout (bin decisions identical to the definition's).
+ * Synchronises; refused during graph capture.  Limits: 1 <= n_bins <= 4096;
+ * 16 bytes per bin + 24 per pixel of the longest forest of shared memory. */
+int lya_xi1d(lya_handle* h, const lya_catalog* cat, int32_t n_bins, double r_max, double* num, double* wsum,
+             double* xi, void* stream);
+
 /* Tally of the mixed path's bin-edge flips (Section 2.1 binning done with FP32
  * separations): over the forest pairs kept by the subsample rule of lya_dmat
  * (p_subsample >= 1 keeps all), every pixel pair is binned with the mixed

@@ -43,8 +43,13 @@ class LyaBins3(ctypes.Structure):
     _fields_ = [("n_r", c_int32), ("n_theta", c_int32), ("n_alpha", c_int32), ("r_max", c_double)]
 
 
+class LyaQuasars(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("ra", c_void_p), ("dec", c_void_p), ("dist", c_void_p), ("weight", c_void_p)]
+
+
 H = c_void_p
 CAT = POINTER(LyaCatalog)
+QSO = POINTER(LyaQuasars)
 BINS = POINTER(LyaBins)
 BINS3 = POINTER(LyaBins3)
 
@@ -75,6 +80,10 @@ SIGNATURES = {
     "lya_xi_subsamples": (c_int, [H, CAT, BINS, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xi_covariance": (c_int, [H, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "lya_xi3": (c_int, [H, CAT, BINS3, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lya_xcf": (c_int, [H, CAT, QSO, c_void_p, BINS, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lya_xdmat": (c_int, [H, CAT, QSO, c_void_p, BINS, c_int, c_double, c_uint64, c_void_p, c_void_p,
+                          c_void_p]),
+    "lya_xi1d": (c_int, [H, CAT, c_int32, c_double, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_flip_tally": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
                                POINTER(c_double), POINTER(c_double), c_void_p]),
     "lya_stage_ms": (c_int, [H, c_int32, POINTER(ctypes.c_float)]),

@@ -303,6 +303,82 @@ def lya_xi3(handle: Handle, cat: DeviceCatalog, grid, stream=None):
     return num, wsum, xi
 
 
+class DeviceQuasars:
+    """Quasars resident on the GPU (layout of ``lya_quasars``)."""
+
+    def __init__(self, ra, dec, dist, weight):
+        self.ra = ra.contiguous()
+        self.dec = dec.contiguous()
+        self.dist = dist.contiguous()
+        self.weight = weight.contiguous()
+        for t in (self.ra, self.dec, self.dist):
+            assert t.dtype == torch.float64
+        assert self.weight.dtype == torch.float32
+
+    @property
+    def n(self) -> int:
+        return int(self.ra.shape[0])
+
+    @classmethod
+    def from_host(cls, q, device="cuda") -> "DeviceQuasars":
+        def t(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(device)
+        return cls(t(q.ra, torch.float64), t(q.dec, torch.float64), t(q.dist, torch.float64),
+                   t(q.weight, torch.float32))
+
+    def c(self) -> "_lib.LyaQuasars":
+        return _lib.LyaQuasars(self.n, self.ra.data_ptr(), self.dec.data_ptr(), self.dist.data_ptr(),
+                               self.weight.data_ptr())
+
+
+def _own(forest_qso):
+    if forest_qso is None:
+        return None, None
+    t = forest_qso if isinstance(forest_qso, torch.Tensor) else torch.as_tensor(np.asarray(forest_qso))
+    t = t.to(device="cuda", dtype=torch.int64).contiguous()
+    return t, t.data_ptr()
+
+
+def lya_xcf(handle: Handle, cat: DeviceCatalog, qso: DeviceQuasars, bins, forest_qso=None, stream=None):
+    """Forest x quasar cross-correlation: num, wsum, xi as flat [n_par n_perp]
+    tensors, r_par over [-r_par_max, r_par_max)."""
+    nb = bins.n_par * bins.n_perp
+    num = torch.empty(nb, dtype=torch.float64, device="cuda")
+    wsum = torch.empty_like(num)
+    xi = torch.empty_like(num)
+    keep, own = _own(forest_qso)
+    c, q, b = cat.c(), qso.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xcf(handle.h, ctypes.byref(c), ctypes.byref(q), own, ctypes.byref(b),
+                                        _ptr(num), _ptr(wsum), _ptr(xi), _stream(stream)))
+    return num, wsum, xi
+
+
+def lya_xdmat(handle: Handle, cat: DeviceCatalog, qso: DeviceQuasars, bins, p_subsample: float, seed: int,
+              forest_qso=None, eta: str = "mean_slope", stream=None):
+    """Distortion matrix of the cross-correlation: D [nb, nb] and W_A [nb]."""
+    nb = bins.n_par * bins.n_perp
+    D = torch.empty((nb, nb), dtype=torch.float64, device="cuda")
+    W = torch.empty(nb, dtype=torch.float64, device="cuda")
+    keep, own = _own(forest_qso)
+    c, q, b = cat.c(), qso.c(), c_bins(bins)
+    e = _lib.LYA_ETA_IDENTITY if eta == "identity" else _lib.LYA_ETA_MEAN_SLOPE
+    check(handle.h, _lib.load().lya_xdmat(handle.h, ctypes.byref(c), ctypes.byref(q), own, ctypes.byref(b), e,
+                                          float(p_subsample), ctypes.c_uint64(seed), _ptr(D), _ptr(W),
+                                          _stream(stream)))
+    return D, W
+
+
+def lya_xi1d(handle: Handle, cat: DeviceCatalog, n_bins: int, r_max: float, stream=None):
+    """Same-forest correlation: num, wsum, xi as [n_bins] tensors."""
+    num = torch.empty(int(n_bins), dtype=torch.float64, device="cuda")
+    wsum = torch.empty_like(num)
+    xi = torch.empty_like(num)
+    c = cat.c()
+    check(handle.h, _lib.load().lya_xi1d(handle.h, ctypes.byref(c), int(n_bins), float(r_max), _ptr(num),
+                                         _ptr(wsum), _ptr(xi), _stream(stream)))
+    return num, wsum, xi
+
+
 def lya_flip_tally(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float = 1.0, seed: int = 0,
                    stream=None):
     n, f = ctypes.c_int64(), ctypes.c_int64()

@@ -141,6 +141,15 @@ struct lya_handle {
   size_t out_cap = 0;
   void* gbuf = nullptr;        // D accumulator
   size_t g_cap = 0;
+  // quasars of the cross-correlation and the (forest, quasar) pair list
+  void* qbuf = nullptr;
+  size_t qbuf_cap = 0;
+  Forests Q{};
+  int2* xpairs = nullptr;
+  int64_t xpair_cap = 0;
+  int64_t n_xpairs = 0;
+  void* xqoff = nullptr;       // [n_forests + 1] start of each forest's quasars in xpairs
+  size_t xqoff_cap = 0;
   // tuning and diagnostics
   int tuned_warps = 8;
   int tuned_grab = 4;
@@ -530,7 +539,7 @@ int lya_destroy(lya_handle* h) {
   *h->alive = false;   // graphs captured on this handle refuse to launch from now on
   cudaDeviceSynchronize();
   void* bufs[] = {h->fbuf, h->pixbuf, h->pairbuf, h->csbuf, h->scratch, h->scratch2, h->outbuf, h->gbuf,
-                  h->forder, h->d_err};
+                  h->forder, h->d_err, h->qbuf, h->xpairs, h->xqoff};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int k = 0; k < 4; ++k)
@@ -1002,6 +1011,205 @@ int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double
   stage_begin(h, 0, s);
   CK(run_xi3(A, h->dev, &h->scratch2, &h->scratch2_cap, h->d_err, s), "xi3");
   stage_end(h, 0, s);
+  return LYA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// forest x quasar cross-correlation, its distortion matrix, 1D correlation
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+int prepare_quasars(lya_handle* h, const lya_quasars* q, cudaStream_t s) {
+  if (!q) return fail(h, LYA_ERR_INVALID_ARG, "quasars is NULL");
+  if (q->n < 0) return fail(h, LYA_ERR_INVALID_ARG, "negative quasar count");
+  if (q->n >= (1LL << 31) - 1) return fail(h, LYA_ERR_TOO_LARGE, "more than 2^31-2 quasars");
+  if (q->n > 0 && (!q->ra || !q->dec || !q->dist || !q->weight))
+    return fail(h, LYA_ERR_INVALID_ARG, "quasar array is NULL");
+  const int64_t n = std::max<int64_t>(q->n, 1);
+  const size_t bytes = static_cast<size_t>(n) * (8 * 4 + 4) + 8 * 256;
+  cudaError_t e = grow(&h->qbuf, &h->qbuf_cap, bytes);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "quasar workspace");
+  char* p = static_cast<char*>(h->qbuf);
+  auto take = [&](size_t b) { char* r = p; p += (b + 255) & ~size_t(255); return r; };
+  Forests Q{};
+  Q.n = q->n;
+  Q.ux = reinterpret_cast<double*>(take(n * 8));
+  Q.uy = reinterpret_cast<double*>(take(n * 8));
+  Q.uz = reinterpret_cast<double*>(take(n * 8));
+  Q.dmin = reinterpret_cast<double*>(take(n * 8));
+  Q.dmax = Q.dmin;
+  Q.len = reinterpret_cast<int32_t*>(take(n * 4));
+  h->Q = Q;
+  CK(launch_qso_prep(*q, Q, h->d_err, s), "quasar prep");
+  return LYA_OK;
+}
+
+unsigned long long dmin_bits(lya_handle* h, const Forests& F, cudaStream_t s) {
+  unsigned long long bits = ~0ull;
+  if (cudaMemsetAsync(h->d_u64, 0xff, 8, s) != cudaSuccess) return bits;
+  if (F.n > 0) {
+    const int64_t blocks = std::min<int64_t>((F.n + 255) / 256, 4096);
+    LYA_COUNT(1), min_dmin_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(F, h->d_u64);
+  }
+  if (cudaMemcpyAsync(&bits, h->d_u64, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return ~0ull;
+  cudaStreamSynchronize(s);
+  return bits;
+}
+
+// Prepare forests and quasars, check their flags, build the (forest, quasar) pair list.
+int build_xpairs(lya_handle* h, const lya_catalog* cat, const lya_quasars* q, const int64_t* forest_qso,
+                 const lya_bins* b, int* max_len, cudaStream_t s) {
+  int st = prepare(h, cat, 1, s);
+  if (st) return st;
+  if ((st = prepare_quasars(h, q, s))) return st;
+  CK(launch_max_len(h->F, h->d_i32, s), "max_len");
+  int32_t ml = 0;
+  CK(cudaMemcpyAsync(&ml, h->d_i32, 4, cudaMemcpyDeviceToHost, s), "read max_len");
+  unsigned flags = 0;
+  if ((st = read_flags(h, s, &flags))) return st;
+  if ((st = flags_to_status(h, flags))) return st;
+  *max_len = ml;
+  double dmf = 1.0, dmq = 1.0;
+  const unsigned long long bf = dmin_bits(h, h->F, s), bq = dmin_bits(h, h->Q, s);
+  if (bf != ~0ull) std::memcpy(&dmf, &bf, 8);
+  if (bq != ~0ull) std::memcpy(&dmq, &bq, 8);
+  const double th = 2.0 * std::asin(std::min(1.0, b->r_perp_max / (dmf + dmq)));
+  const double th_deg = th * 180.0 / M_PI;
+  int nside = 1;
+  while (nside < 256 && 117.0 / th_deg >= 2.0 * nside) nside *= 2;
+  stage_begin(h, 3, s);
+  cudaError_t e = grow(&h->xqoff, &h->xqoff_cap, static_cast<size_t>(h->F.n + 1) * 8);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "forest-quasar offsets");
+  CK(build_cross_pairs(h->F, h->Q, nside, b->r_par_max, b->r_perp_max, forest_qso, &h->xpairs, &h->xpair_cap,
+                       static_cast<int64_t*>(h->xqoff), &h->n_xpairs, s),
+     "forest-quasar pairs");
+  stage_end(h, 3, s);
+  h->last_pairs = h->n_xpairs;
+  return LYA_OK;
+}
+
+XcfArgs xcf_args(lya_handle* h, const lya_catalog* cat, const lya_quasars* q, const lya_bins* b, int max_len) {
+  XcfArgs A{};
+  A.pairs = h->xpairs;
+  A.qoff = static_cast<const int64_t*>(h->xqoff);
+  A.n_pairs = h->n_xpairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.Q = h->Q;
+  A.wq = q->weight;
+  A.delta = cat->delta;
+  A.weight = cat->weight;
+  A.n_par = b->n_par;
+  A.n_perp = b->n_perp;
+  A.r_par_max = b->r_par_max;
+  A.r_perp_max = b->r_perp_max;
+  A.max_len = max_len;
+  return A;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lya_xcf(lya_handle* h, const lya_catalog* cat, const lya_quasars* qso, const int64_t* forest_qso,
+            const lya_bins* bins, double* num, double* wsum, double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!num || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "num and wsum are required");
+  const int nb = bins->n_par * bins->n_perp;
+  if (xcf_smem_bytes(nb, 1) > h->dev.smem_optin)
+    return fail(h, LYA_ERR_TOO_LARGE, "cross-correlation grid above the shared-memory histogram (16 bytes per bin)");
+  if ((st = refuse_in_capture(h, "lya_xcf"))) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int ml = 0;
+  if ((st = build_xpairs(h, cat, qso, forest_qso, bins, &ml, s))) return st;
+  if (xcf_smem_bytes(nb, ml) > h->dev.smem_optin)
+    return fail(h, LYA_ERR_TOO_LARGE, "cross-correlation: 16 bytes per bin + 20 per pixel of the longest forest above shared memory");
+  CK(cudaMemsetAsync(num, 0, static_cast<size_t>(nb) * 8, s), "zero num");
+  CK(cudaMemsetAsync(wsum, 0, static_cast<size_t>(nb) * 8, s), "zero wsum");
+  XcfArgs A = xcf_args(h, cat, qso, bins, ml);
+  A.num = num;
+  A.wsum = wsum;
+  stage_begin(h, 0, s);
+  CK(launch_xcf(A, h->dev, s), "cross-correlation kernel");
+  stage_end(h, 0, s);
+  if (xi) CK(launch_finalize(num, wsum, xi, nb, s), "finalize");
+  return LYA_OK;
+}
+
+int lya_xdmat(lya_handle* h, const lya_catalog* cat, const lya_quasars* qso, const int64_t* forest_qso,
+              const lya_bins* bins, lya_eta eta, double p_subsample, uint64_t seed, double* dmat, double* wsum_dm,
+              void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!dmat) return fail(h, LYA_ERR_INVALID_ARG, "dmat is NULL");
+  if (eta != LYA_ETA_IDENTITY && eta != LYA_ETA_MEAN_SLOPE) return fail(h, LYA_ERR_INVALID_ARG, "unknown eta");
+  if (!(p_subsample >= 0.0 && p_subsample <= 1.0))
+    return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must lie in [0, 1]");
+  if ((st = refuse_in_capture(h, "lya_xdmat"))) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int ml = 0;
+  if ((st = build_xpairs(h, cat, qso, forest_qso, bins, &ml, s))) return st;
+  if (xdm_warps(h->dev, ml) < 1)
+    return fail(h, LYA_ERR_TOO_LARGE, "forests too long for the cross distortion matrix (20 bytes per pixel per warp)");
+  const int nb = bins->n_par * bins->n_perp;
+  const size_t nb2 = static_cast<size_t>(nb) * nb;
+  cudaError_t e = grow(&h->gbuf, &h->g_cap, (nb2 + nb) * 8);
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "distortion-matrix accumulator");
+  double* G = static_cast<double*>(h->gbuf);
+  double* wdm = G + nb2;
+  CK(cudaMemsetAsync(G, 0, (nb2 + nb) * 8, s), "zero accumulator");
+  XcfArgs A = xcf_args(h, cat, qso, bins, ml);
+  A.eta_mean_slope = (eta == LYA_ETA_MEAN_SLOPE);
+  A.p_subsample = p_subsample;
+  A.seed = seed;
+  A.G = G;
+  A.wdm = wdm;
+  stage_begin(h, 1, s);
+  CK(launch_xdm(A, h->dev, s), "cross distortion-matrix kernel");
+  stage_end(h, 1, s);
+  CK(launch_dm_finalize(G, wdm, dmat, wsum_dm, nb, 1, s), "finalize");
+  return LYA_OK;
+}
+
+int lya_xi1d(lya_handle* h, const lya_catalog* cat, int32_t n_bins, double r_max, double* num, double* wsum,
+             double* xi, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (n_bins < 1 || n_bins > 4096) return fail(h, LYA_ERR_TOO_LARGE, "1D grid outside 1..4096 bins");
+  if (!(r_max > 0) || !std::isfinite(r_max)) return fail(h, LYA_ERR_INVALID_ARG, "r_max must be finite and > 0");
+  if (!num || !wsum) return fail(h, LYA_ERR_INVALID_ARG, "num and wsum are required");
+  int st = refuse_in_capture(h, "lya_xi1d");
+  if (st) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = prepare(h, cat, 1, s))) return st;
+  CK(launch_max_len(h->F, h->d_i32, s), "max_len");
+  int32_t ml = 0;
+  CK(cudaMemcpyAsync(&ml, h->d_i32, 4, cudaMemcpyDeviceToHost, s), "read max_len");
+  unsigned flags = 0;
+  if ((st = read_flags(h, s, &flags))) return st;
+  if ((st = flags_to_status(h, flags))) return st;
+  if (xi1d_smem_bytes(n_bins, ml) > h->dev.smem_optin)
+    return fail(h, LYA_ERR_TOO_LARGE, "1D correlation: 16 bytes per bin + 24 per pixel of the longest forest above shared memory");
+  CK(cudaMemsetAsync(num, 0, static_cast<size_t>(n_bins) * 8, s), "zero num");
+  CK(cudaMemsetAsync(wsum, 0, static_cast<size_t>(n_bins) * 8, s), "zero wsum");
+  X1Args A{};
+  A.F = h->F;
+  A.dist = cat->dist;
+  A.delta = cat->delta;
+  A.weight = cat->weight;
+  A.n_bins = n_bins;
+  A.r_max = r_max;
+  A.num = num;
+  A.wsum = wsum;
+  A.max_len = ml;
+  stage_begin(h, 0, s);
+  CK(launch_xi1d(A, static_cast<const Pix*>(h->pixbuf), h->dev, s), "1D correlation kernel");
+  stage_end(h, 0, s);
+  if (xi) CK(launch_finalize(num, wsum, xi, n_bins, s), "finalize");
   return LYA_OK;
 }
 

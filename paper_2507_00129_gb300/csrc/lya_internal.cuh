@@ -244,6 +244,59 @@ struct X3Args {
 cudaError_t run_xi3(const X3Args& a, const DevInfo& dev, void** scratch, size_t* scratch_cap, unsigned* err,
                     cudaStream_t s);
 
+// pairs.cu: (forest, quasar) pairs that can hold an in-grid pixel, forest
+// f's own quasar own[f] excluded (own may be NULL), grouped by forest:
+// forest f's pairs are (*pairs)[qoff[f] .. qoff[f+1]) (qoff: device [F.n+1]).
+// Q is a point set in the Forests layout (ux, uy, uz, dmin = dmax = distance,
+// len = 1 or 0 = invalid).  *pairs is grown with cudaMalloc as needed.
+// Synchronises.
+cudaError_t build_cross_pairs(const Forests& F, const Forests& Q, int nside, double rpar_max, double rperp_max,
+                              const int64_t* own, int2** pairs, int64_t* cap, int64_t* qoff, int64_t* n_out,
+                              cudaStream_t s);
+
+// xcf.cu: forest x quasar cross-correlation, its distortion matrix, and the
+// same-forest (1D) correlation
+struct XcfArgs {
+  const int2* pairs;     // (forest, quasar), grouped by forest
+  const int64_t* qoff;   // [F.n + 1] forest f's pairs: qoff[f] .. qoff[f+1]
+  int64_t n_pairs;
+  const float* delta;    // caller's pixel arrays (single catalogue: packed index = pixel index)
+  const float* weight;
+  const Pix* pix;
+  Forests F;
+  Forests Q;
+  const float* wq;       // quasar weights
+  int n_par, n_perp;     // r_par over [-r_par_max, r_par_max) in n_par bins
+  double r_par_max, r_perp_max;
+  double* num;           // [nb] cross-correlation sums
+  double* wsum;
+  int eta_mean_slope;    // distortion matrix
+  double p_subsample;
+  uint64_t seed;
+  double* G;             // [nb*nb] upper triangle (A <= B) of D~
+  double* wdm;           // [nb]
+  int max_len;
+};
+cudaError_t launch_qso_prep(const lya_quasars& q, Forests Q, unsigned* err, cudaStream_t s);
+cudaError_t launch_xcf(const XcfArgs& a, const DevInfo& dev, cudaStream_t s);
+cudaError_t launch_xdm(const XcfArgs& a, const DevInfo& dev, cudaStream_t s);
+// shared memory the kernels need: 0 when the grid or forest length is beyond their limits
+int xcf_smem_bytes(int nb, int max_len);
+int xdm_warps(const DevInfo& dev, int max_len);
+struct X1Args {
+  Forests F;
+  const double* dist;    // caller's arrays (single catalogue: packed index = pixel index)
+  const float* delta;
+  const float* weight;
+  int n_bins;
+  double r_max;
+  double* num;
+  double* wsum;
+  int max_len;
+};
+int xi1d_smem_bytes(int n_bins, int max_len);
+cudaError_t launch_xi1d(const X1Args& a, const Pix* pix, const DevInfo& dev, cudaStream_t s);
+
 // scratch helper (api.cu).  While the calling thread captures a CUDA graph
 // (lya_capture_begin) it allocates nothing and fails with
 // cudaErrorNotPermitted if the buffer is too small.

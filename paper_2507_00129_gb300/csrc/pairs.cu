@@ -377,6 +377,93 @@ __global__ void band_scatter_kernel(const int2* pairs, const float2* cs, int64_t
   }
 }
 
+// ---- forest x quasar pairs: cells of the forests against cells of the quasars
+
+// one warp per forest cell c1, all quasar cells c2; MODE 0 counts, MODE 1 fills
+template <int MODE>
+__global__ void cross_cell_pair_kernel(const CellStat* sf, int64_t KF, const CellStat* sq, int64_t KQ,
+                                       double rperp_max, int32_t* row_count, const int64_t* row_off, int2* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c1 = warp; c1 < KF; c1 += nw) {
+    const CellStat p = sf[c1];
+    int64_t run = (MODE == 1) ? row_off[c1] : 0;
+    int32_t cnt = 0;
+    for (int64_t base = 0; base < KQ; base += 32) {
+      const int64_t c2 = base + lane;
+      const bool ok = (c2 < KQ) && cells_may_pair(p, sq[c2], rperp_max);
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (MODE == 1 && ok) out[run + __popc(m & ((1u << lane) - 1u))] = make_int2(static_cast<int>(c1), static_cast<int>(c2));
+      run += __popc(m);
+      cnt += __popc(m);
+    }
+    if (MODE == 0 && lane == 0) row_count[c1] = cnt;
+  }
+}
+
+// Forest a and quasar q can hold an in-grid pixel: r_perp >= (d_first + d_q) sin(theta/2) and
+// |r_par| >= (distance from d_q to the forest's distance range) cos(theta/2), both exact bounds.
+__device__ __forceinline__ bool forest_quasar_pair(const Forests& F, int32_t a, const Forests& Q, int32_t q,
+                                                   double rpar_max, double rperp_max) {
+  const double ax = F.ux[a], ay = F.uy[a], az = F.uz[a];
+  const double qx = Q.ux[q], qy = Q.uy[q], qz = Q.uz[q];
+  const double dx = ax - qx, dy = ay - qy, dz = az - qz;
+  const double sx = ax + qx, sy = ay + qy, sz = az + qz;
+  const double s = 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
+  const double c = 0.5 * sqrt(sx * sx + sy * sy + sz * sz);
+  if ((F.dmin[a] + Q.dmin[q]) * s >= rperp_max) return false;
+  const double gap = fmax(0.0, fmax(Q.dmin[q] - F.dmax[a], F.dmin[a] - Q.dmin[q]));
+  return gap * c < rpar_max;
+}
+
+// one warp per (forest cell, quasar cell) pair; MODE 0 counts, MODE 1 fills (forest, quasar)
+template <int MODE>
+__global__ void cross_member_kernel(Forests F, Forests Q, const CellStat* sf, const CellStat* sq, const int2* cp,
+                                    int64_t ncp, const int32_t* mf, const int32_t* mq, double rpar_max,
+                                    double rperp_max, const int64_t* own, int32_t* cnt_out, const int64_t* off,
+                                    int2* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = warp; k < ncp; k += nw) {
+    const int2 c = cp[k];
+    const CellStat p = sf[c.x], q = sq[c.y];
+    int64_t run = (MODE == 1) ? off[k] : 0;
+    int32_t cnt = 0;
+    for (int ia = 0; ia < p.n; ++ia) {
+      const int32_t fa = mf[p.begin + ia];
+      const int64_t own_q = own ? own[fa] : -1;
+      for (int ib0 = 0; ib0 < q.n; ib0 += 32) {
+        const int ib = ib0 + lane;
+        bool ok = false;
+        int32_t fq = 0;
+        if (ib < q.n) {
+          fq = mq[q.begin + ib];
+          ok = (fq != own_q) && forest_quasar_pair(F, fa, Q, fq, rpar_max, rperp_max);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (MODE == 1 && ok) out[run + __popc(m & ((1u << lane) - 1u))] = make_int2(fa, fq);
+        run += __popc(m);
+        cnt += __popc(m);
+      }
+    }
+    if (MODE == 0 && lane == 0) cnt_out[k] = cnt;
+  }
+}
+
+__global__ void xcount_kernel(const int2* p, int64_t n, int32_t* count) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&count[p[k].x], 1);
+}
+
+__global__ void xscatter_kernel(const int2* p, int64_t n, const int64_t* start, int32_t* cursor, int2* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 v = p[k];
+    out[start[v.x] + atomicAdd(&cursor[v.x], 1)] = v;
+  }
+}
+
 int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -566,6 +653,146 @@ cudaError_t launch_unpack_pairs(const int2* p, int64_t n, int32_t* a, int32_t* b
   if (n == 0) return cudaSuccess;
   LYA_COUNT(1), unpack_pairs_kernel<<<grid_for(n, kT), kT, 0, s>>>(p, n, a, b);
   return cudaGetLastError();
+}
+
+}  // namespace lya
+
+namespace lya {
+namespace {
+
+// HEALPix cell index of one point set (forests or quasars): members sorted by
+// cell and the statistics of the occupied cells.  One device allocation.
+struct CellIndex {
+  void* buf = nullptr;
+  int32_t* members = nullptr;
+  CellStat* st = nullptr;
+  int64_t K = 0;
+};
+
+cudaError_t index_cells(const Forests& F, int nside, CellIndex* ci, cudaStream_t s) {
+  const int64_t nf = F.n;
+  const int64_t ncells = 12LL * nside * nside;
+  auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t o_cell = 0;
+  const size_t o_count = o_cell + al(nf * 4);
+  const size_t o_cursor = o_count + al(ncells * 4);
+  const size_t o_start = o_cursor + al(ncells * 4);
+  const size_t o_members = o_start + al((ncells + 1) * 8);
+  const size_t o_flag = o_members + al(nf * 4);
+  const size_t o_fpos = o_flag + al(ncells * 4);
+  const size_t o_occ = o_fpos + al((ncells + 1) * 8);
+  const size_t o_stat = o_occ + al(ncells * 4);
+  const size_t o_end = o_stat + al(sizeof(CellStat) * (size_t)std::max<int64_t>(1, std::min<int64_t>(ncells, nf)));
+  LYA_TRY(cudaMallocAsync(&ci->buf, o_end, s));
+  char* sc = static_cast<char*>(ci->buf);
+  int32_t* cell = reinterpret_cast<int32_t*>(sc + o_cell);
+  int32_t* count = reinterpret_cast<int32_t*>(sc + o_count);
+  int32_t* cursor = reinterpret_cast<int32_t*>(sc + o_cursor);
+  int64_t* start = reinterpret_cast<int64_t*>(sc + o_start);
+  ci->members = reinterpret_cast<int32_t*>(sc + o_members);
+  int32_t* flag = reinterpret_cast<int32_t*>(sc + o_flag);
+  int64_t* fpos = reinterpret_cast<int64_t*>(sc + o_fpos);
+  int32_t* occ = reinterpret_cast<int32_t*>(sc + o_occ);
+  ci->st = reinterpret_cast<CellStat*>(sc + o_stat);
+  LYA_TRY(cudaMemsetAsync(count, 0, ncells * 4, s));
+  LYA_TRY(cudaMemsetAsync(cursor, 0, ncells * 4, s));
+  LYA_COUNT(1), cell_kernel<<<grid_for(nf, kT), kT, 0, s>>>(F, 0, nf, nside, cell, count);
+  LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(count, ncells, start);
+  LYA_COUNT(1), scatter_kernel<<<grid_for(nf, kT), kT, 0, s>>>(cell, 0, nf, start, cursor, ci->members);
+  LYA_COUNT(1), cell_sort_kernel<<<grid_for(ncells, kT), kT, 0, s>>>(start, ncells, ci->members);
+  LYA_COUNT(1), occupied_flags<<<grid_for(ncells, kT), kT, 0, s>>>(count, ncells, flag);
+  LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(flag, ncells, fpos);
+  LYA_COUNT(1), occupied_list<<<grid_for(ncells, kT), kT, 0, s>>>(count, fpos, ncells, occ);
+  LYA_TRY(cudaGetLastError());
+  LYA_TRY(cudaMemcpyAsync(&ci->K, fpos + ncells, 8, cudaMemcpyDeviceToHost, s));
+  LYA_TRY(cudaStreamSynchronize(s));
+  if (ci->K > 0) {
+    LYA_COUNT(1), cell_stat_kernel<<<grid_for(ci->K * 32, kT), kT, 0, s>>>(F, occ, ci->K, start, ci->members, ci->st);
+    LYA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t build_cross_pairs(const Forests& F, const Forests& Q, int nside, double rpar_max, double rperp_max,
+                              const int64_t* own, int2** pairs, int64_t* cap, int64_t* qoff, int64_t* n_out,
+                              cudaStream_t s) {
+  *n_out = 0;
+  LYA_TRY(cudaMemsetAsync(qoff, 0, (F.n + 1) * 8, s));
+  if (F.n == 0 || Q.n == 0) return cudaSuccess;
+  int2* unsorted = nullptr;
+  int32_t* fcount = nullptr;
+  CellIndex cf, cq;
+  int32_t* row_count = nullptr;
+  int64_t* row_off = nullptr;
+  int2* cpairs = nullptr;
+  int32_t* pc = nullptr;
+  int64_t* poff = nullptr;
+  int64_t M = 0, P = 0;
+  cudaError_t err = index_cells(F, nside, &cf, s);
+  if (err == cudaSuccess) err = index_cells(Q, nside, &cq, s);
+  if (err == cudaSuccess && cf.K > 0 && cq.K > 0) {
+    err = cudaMallocAsync(reinterpret_cast<void**>(&row_count), cf.K * 4, s);
+    if (err == cudaSuccess) err = cudaMallocAsync(reinterpret_cast<void**>(&row_off), (cf.K + 1) * 8, s);
+    if (err == cudaSuccess) {
+      LYA_COUNT(1), cross_cell_pair_kernel<0><<<grid_for(cf.K * 32, kT), kT, 0, s>>>(cf.st, cf.K, cq.st, cq.K,
+                                                                           rperp_max, row_count, nullptr, nullptr);
+      LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(row_count, cf.K, row_off);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaMemcpyAsync(&M, row_off + cf.K, 8, cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err == cudaSuccess && M > 0) {
+      err = cudaMallocAsync(reinterpret_cast<void**>(&cpairs), M * sizeof(int2), s);
+      if (err == cudaSuccess) err = cudaMallocAsync(reinterpret_cast<void**>(&pc), M * 4, s);
+      if (err == cudaSuccess) err = cudaMallocAsync(reinterpret_cast<void**>(&poff), (M + 1) * 8, s);
+      if (err == cudaSuccess) {
+        LYA_COUNT(1), cross_cell_pair_kernel<1><<<grid_for(cf.K * 32, kT), kT, 0, s>>>(cf.st, cf.K, cq.st, cq.K,
+                                                                             rperp_max, nullptr, row_off, cpairs);
+        LYA_COUNT(1), cross_member_kernel<0><<<grid_for(M * 32, kT), kT, 0, s>>>(
+            F, Q, cf.st, cq.st, cpairs, M, cf.members, cq.members, rpar_max, rperp_max, own, pc, nullptr, nullptr);
+        LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(pc, M, poff);
+        err = cudaGetLastError();
+      }
+      if (err == cudaSuccess) err = cudaMemcpyAsync(&P, poff + M, 8, cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err == cudaSuccess && P > *cap) {
+        int64_t ncap = std::max<int64_t>(P, (*cap) * 3 / 2);
+        if (*pairs) { cudaFree(*pairs); *pairs = nullptr; *cap = 0; }
+        err = cudaMalloc(reinterpret_cast<void**>(pairs), ncap * sizeof(int2));
+        if (err == cudaSuccess) *cap = ncap; else *pairs = nullptr;
+      }
+      if (err == cudaSuccess && P > 0) err = cudaMallocAsync(reinterpret_cast<void**>(&unsorted), P * sizeof(int2), s);
+      if (err == cudaSuccess && P > 0) err = cudaMallocAsync(reinterpret_cast<void**>(&fcount), F.n * 8, s);
+      if (err == cudaSuccess && P > 0) {
+        LYA_COUNT(1), cross_member_kernel<1><<<grid_for(M * 32, kT), kT, 0, s>>>(
+            F, Q, cf.st, cq.st, cpairs, M, cf.members, cq.members, rpar_max, rperp_max, own, nullptr, poff, unsorted);
+        // group by forest: counting sort into *pairs, qoff[f] .. qoff[f+1] = forest f's quasars
+        int32_t* cursor = fcount + F.n;
+        err = cudaMemsetAsync(fcount, 0, F.n * 8, s);
+        if (err == cudaSuccess) {
+          LYA_COUNT(1), xcount_kernel<<<grid_for(P, kT), kT, 0, s>>>(unsorted, P, fcount);
+          LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(fcount, F.n, qoff);
+          LYA_COUNT(1), xscatter_kernel<<<grid_for(P, kT), kT, 0, s>>>(unsorted, P, qoff, cursor, *pairs);
+          err = cudaGetLastError();
+        }
+      }
+    }
+  }
+  if (unsorted) cudaFreeAsync(unsorted, s);
+  if (fcount) cudaFreeAsync(fcount, s);
+  if (cpairs) cudaFreeAsync(cpairs, s);
+  if (pc) cudaFreeAsync(pc, s);
+  if (poff) cudaFreeAsync(poff, s);
+  if (row_count) cudaFreeAsync(row_count, s);
+  if (row_off) cudaFreeAsync(row_off, s);
+  if (cf.buf) cudaFreeAsync(cf.buf, s);
+  if (cq.buf) cudaFreeAsync(cq.buf, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (err == cudaSuccess) err = e2;
+  *n_out = (err == cudaSuccess) ? P : 0;
+  return err;
 }
 
 }  // namespace lya
