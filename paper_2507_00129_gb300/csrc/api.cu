@@ -150,6 +150,10 @@ struct lya_handle {
   int64_t n_xpairs = 0;
   void* xqoff = nullptr;       // [n_forests + 1] start of each forest's quasars in xpairs
   size_t xqoff_cap = 0;
+  bool xpairs_valid = false;   // cached (forest, quasar) list: key + forest and quasar fingerprints
+  CatKey xkey;
+  unsigned long long x_fp = 0, x_qfp = 0;
+  unsigned long long* d_qfp = nullptr;
   // tuning and diagnostics
   int tuned_warps = 8;
   int tuned_grab = 4;
@@ -258,6 +262,7 @@ int flags_to_status(lya_handle* h, unsigned f) {
   int code = LYA_ERR_DEVICE_CHECK;
   if (f & FLAG_OFFSETS) { m += " inconsistent offsets or pair indices;"; code = LYA_ERR_DEVICE_CHECK; }
   if (f & FLAG_TOO_LONG) { m += " forest longer than 2^20 pixels;"; code = LYA_ERR_TOO_LARGE; }
+  if (f & FLAG_RETRY) { m += " a shared-memory update exceeded its retry limit;"; code = LYA_ERR_TIMEOUT; }
   if (f & FLAG_X3_CAP) { m += " a 3PCF main vertex has more neighbours within r_max than the kernel holds;"; code = LYA_ERR_TOO_LARGE; }
   if (f & FLAG_NEGATIVE_W) { m += " negative weight;"; code = LYA_ERR_NONFINITE; }
   if (f & FLAG_NONFINITE) { m += " non-finite or non-positive value;"; code = LYA_ERR_NONFINITE; }
@@ -524,6 +529,7 @@ int lya_create(lya_handle** out) {
   h->d_i32 = reinterpret_cast<int32_t*>(p + 128);
   h->d_u64 = reinterpret_cast<unsigned long long*>(p + 192);
   h->d_fp = reinterpret_cast<unsigned long long*>(p + 256);
+  h->d_qfp = reinterpret_cast<unsigned long long*>(p + 320);
   *out = h;
   return LYA_OK;
 }
@@ -1042,7 +1048,7 @@ int prepare_quasars(lya_handle* h, const lya_quasars* q, cudaStream_t s) {
   Q.dmax = Q.dmin;
   Q.len = reinterpret_cast<int32_t*>(take(n * 4));
   h->Q = Q;
-  CK(launch_qso_prep(*q, Q, h->d_err, s), "quasar prep");
+  CK(launch_qso_prep(*q, Q, h->d_err, h->d_qfp, s), "quasar prep");
   return LYA_OK;
 }
 
@@ -1063,14 +1069,31 @@ int build_xpairs(lya_handle* h, const lya_catalog* cat, const lya_quasars* q, co
                  const lya_bins* b, int* max_len, cudaStream_t s) {
   int st = prepare(h, cat, 1, s);
   if (st) return st;
+  CK(cudaMemsetAsync(h->d_qfp, 0, 8, s), "clear quasar fingerprint");
   if ((st = prepare_quasars(h, q, s))) return st;
+  CK(launch_own_hash(forest_qso, cat->n_forests, h->d_qfp, s), "own-quasar hash");
   CK(launch_max_len(h->F, h->d_i32, s), "max_len");
   int32_t ml = 0;
+  unsigned long long fp = 0, qfp = 0;
   CK(cudaMemcpyAsync(&ml, h->d_i32, 4, cudaMemcpyDeviceToHost, s), "read max_len");
+  CK(cudaMemcpyAsync(&fp, h->d_fp, 8, cudaMemcpyDeviceToHost, s), "read fingerprint");
+  CK(cudaMemcpyAsync(&qfp, h->d_qfp, 8, cudaMemcpyDeviceToHost, s), "read quasar fingerprint");
   unsigned flags = 0;
   if ((st = read_flags(h, s, &flags))) return st;
   if ((st = flags_to_status(h, flags))) return st;
   *max_len = ml;
+  // reuse the list built for the same pointers, sizes, bins and geometry (see ensure_pairs)
+  CatKey key = make_key(cat, 1, b);
+  key.ptrs.push_back(q->ra);
+  key.ptrs.push_back(q->dec);
+  key.ptrs.push_back(q->dist);
+  key.ptrs.push_back(forest_qso);
+  key.sizes.push_back(q->n);
+  if (h->xpairs_valid && h->xkey == key && h->x_fp == fp && h->x_qfp == qfp) {
+    h->last_pairs = h->n_xpairs;
+    return LYA_OK;
+  }
+  h->xpairs_valid = false;
   double dmf = 1.0, dmq = 1.0;
   const unsigned long long bf = dmin_bits(h, h->F, s), bq = dmin_bits(h, h->Q, s);
   if (bf != ~0ull) std::memcpy(&dmf, &bf, 8);
@@ -1087,6 +1110,10 @@ int build_xpairs(lya_handle* h, const lya_catalog* cat, const lya_quasars* q, co
      "forest-quasar pairs");
   stage_end(h, 3, s);
   h->last_pairs = h->n_xpairs;
+  h->xkey = key;
+  h->x_fp = fp;
+  h->x_qfp = qfp;
+  h->xpairs_valid = true;
   return LYA_OK;
 }
 
@@ -1106,6 +1133,7 @@ XcfArgs xcf_args(lya_handle* h, const lya_catalog* cat, const lya_quasars* q, co
   A.r_par_max = b->r_par_max;
   A.r_perp_max = b->r_perp_max;
   A.max_len = max_len;
+  A.err = h->d_err;
   return A;
 }
 

@@ -16,6 +16,7 @@ enum : unsigned {
   FLAG_NEGATIVE_W = 8u,
   FLAG_TOO_LONG = 16u,
   FLAG_X3_CAP = 32u,      // a 3PCF main vertex had more neighbours than the kernel's capacity
+  FLAG_RETRY = 64u,       // a shared-memory compare-and-swap update gave up after its retry limit
 };
 
 // Per-forest data derived by the preparation kernel (structure of arrays).
@@ -270,6 +271,7 @@ struct XcfArgs {
   double r_par_max, r_perp_max;
   double* num;           // [nb] cross-correlation sums
   double* wsum;
+  unsigned* err;         // device flags
   int eta_mean_slope;    // distortion matrix
   double p_subsample;
   uint64_t seed;
@@ -277,7 +279,11 @@ struct XcfArgs {
   double* wdm;           // [nb]
   int max_len;
 };
-cudaError_t launch_qso_prep(const lya_quasars& q, Forests Q, unsigned* err, cudaStream_t s);
+// fp accumulates a fingerprint of the quasars' geometry (index, position, distance, validity)
+cudaError_t launch_qso_prep(const lya_quasars& q, Forests Q, unsigned* err, unsigned long long* fp,
+                            cudaStream_t s);
+// adds a fingerprint of own[0..n) (own-quasar indices; nothing for NULL) to *fp
+cudaError_t launch_own_hash(const int64_t* own, int64_t n, unsigned long long* fp, cudaStream_t s);
 cudaError_t launch_xcf(const XcfArgs& a, const DevInfo& dev, cudaStream_t s);
 cudaError_t launch_xdm(const XcfArgs& a, const DevInfo& dev, cudaStream_t s);
 // shared memory the kernels need: 0 when the grid or forest length is beyond their limits

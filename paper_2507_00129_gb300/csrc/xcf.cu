@@ -39,7 +39,8 @@
 namespace lya {
 namespace {
 
-constexpr int kXW = 8;   // warps per block
+constexpr int kXW = 8;    // warps per block (distortion matrix)
+constexpr int kXCW = 16;  // warps per block of the cross-correlation (two blocks per SM share the shared memory)
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -114,7 +115,13 @@ __device__ __forceinline__ bool run_scan(int bin, int lane, float& h1, float& l1
   return bin >= 0 && (lane == 31 || nxt != bin);
 }
 
-__global__ void qso_prep_kernel(lya_quasars q, Forests Q, unsigned* err) {
+__global__ void own_hash_kernel(const int64_t* own, int64_t n, unsigned long long* fp) {
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n; f += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(fp, static_cast<unsigned long long>(
+                      splitmix64(static_cast<uint64_t>(f) * 0xD1B54A32D192ED03ull ^ static_cast<uint64_t>(own[f]))));
+}
+
+__global__ void qso_prep_kernel(lya_quasars q, Forests Q, unsigned* err, unsigned long long* fp) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < q.n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const double ra = q.ra[k], dec = q.dec[k], d = q.dist[k];
@@ -132,6 +139,12 @@ __global__ void qso_prep_kernel(lya_quasars q, Forests Q, unsigned* err) {
     Q.uz[k] = sd;
     Q.dmin[k] = fin ? d : 1.0;
     Q.len[k] = (fin && w >= 0.0f) ? 1 : 0;
+    auto bits = [](double v) { return static_cast<uint64_t>(__double_as_longlong(v)); };
+    uint64_t x = splitmix64(static_cast<uint64_t>(k) * 0x9E3779B97F4A7C15ull ^ static_cast<uint64_t>(Q.len[k]));
+    x = splitmix64(x ^ bits(ra));
+    x = splitmix64(x ^ bits(dec));
+    x = splitmix64(x ^ bits(d));
+    atomicAdd(fp, static_cast<unsigned long long>(x));
   }
 }
 
@@ -220,40 +233,67 @@ __device__ __forceinline__ int run_start(int bin, int lane) {
   return 31 - __clz(hm & (0xffffffffu >> (31 - lane)));
 }
 
-// One block per forest (grid-stride): the forest's packed distances and FP64
-// prefix sums of w and w delta are staged in shared memory; warps take 32 of
-// the forest's quasars at a time, one pair's geometry per lane, then walk each
-// pair's window together.  A run of equal bins [j0, j1] adds
-// w_q (P[j1+1] - P[j0]) to the block's FP64 histogram.
-__global__ void __launch_bounds__(kXW * 32) xcf_kernel(XcfArgs A, int cap) {
-  extern __shared__ double xsh[];   // [2 nb] histogram | P_w [cap+1] | P_wd [cap+1] | xs [cap] (float)
+// Add the double-float value (h, l) to the double-float pair at p (hi, lo as
+// one 64-bit word) by compare-and-swap; TwoSum keeps the rounding error of the
+// high part in the low part.  Gives up (and flags) after kRetry failed swaps,
+// each of which means another thread's update went through.
+constexpr int kRetry = 1 << 16;
+
+__device__ __forceinline__ void df_atomic_add(float2* p, float h, float l, unsigned* err) {
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
+  unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
+  for (int it = 0; it < kRetry; ++it) {
+    const float2 cur = make_float2(__uint_as_float(static_cast<unsigned>(old)),
+                                   __uint_as_float(static_cast<unsigned>(old >> 32)));
+    float s, e;
+    two_sum(cur.x, h, s, e);
+    const float t = cur.y + l + e;
+    const float H = s + t;
+    const float L = t - (H - s);
+    const unsigned long long nw = static_cast<unsigned long long>(__float_as_uint(H)) |
+                                  (static_cast<unsigned long long>(__float_as_uint(L)) << 32);
+    const unsigned long long seen = atomicCAS(a, old, nw);
+    if (seen == old) return;
+    old = seen;
+  }
+  atomicOr(err, FLAG_RETRY);
+}
+
+// One block per forest (grid-stride): the forest's packed pixels are staged in
+// shared memory; warps take 32 of the forest's quasars at a time, one pair's
+// geometry per lane (FP64), then walk each pair's window together.  Per lane
+// the products w_q w_j and w_q (w delta)_j are exact FP32 pairs (TwoProduct),
+// a segmented TwoSum scan forms each run's sum, and the run's last lane adds
+// it to the block's double-float histogram: no FP64 arithmetic per pixel.
+__global__ void __launch_bounds__(kXCW * 32, 2) xcf_kernel(XcfArgs A, int cap) {
+  extern __shared__ float4 xs4[];   // [nb] (num hi, num lo, w hi, w lo) | staged pixels [cap] | xs [cap]
   const int nb = A.n_par * A.n_perp;
-  double* snum = xsh;
-  double* sw = xsh + nb;
-  double* Pw = xsh + 2 * nb;
-  double* Pwd = Pw + cap + 1;
-  float* xs = reinterpret_cast<float*>(Pwd + cap + 1);
-  for (int k = threadIdx.x; k < 2 * nb; k += blockDim.x) xsh[k] = 0.0;
+  float4* hist = xs4;
+  Pix* sp = xs4 + nb;
+  float* xs = reinterpret_cast<float*>(sp + cap);
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   for (int64_t f = blockIdx.x; f < A.F.n; f += gridDim.x) {
     const int64_t q0 = A.qoff[f], q1 = A.qoff[f + 1];
     const int n = A.F.len[f];
     if (q1 <= q0 || n <= 0 || n > cap) continue;   // uniform over the block
     __syncthreads();                               // the previous forest's readers are done
-    const int64_t o = A.F.off[f];
-    stage_prefix(A.pix + o, n, xs, Pw, Pwd, [&](int k) {
-      const double w = static_cast<double>(A.weight[o + k]);
-      return make_double2(w, w * static_cast<double>(A.delta[o + k]));
-    });
-    for (int64_t qb = q0 + static_cast<int64_t>(wi) * 32; qb < q1; qb += kXW * 32) {
+    const Pix* fp = A.pix + A.F.off[f];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const Pix P = fp[k];
+      sp[k] = P;
+      xs[k] = P.x;
+    }
+    __syncthreads();
+    for (int64_t qb = q0 + static_cast<int64_t>(wi) * 32; qb < q1; qb += kXCW * 32) {
       XGeo g{0.f, 0.f, 0.f, 0.f, 0, 0};
-      double wq = 0.0;
+      float wq = 0.f;
       const int64_t k = qb + lane;
       if (k < q1) {
         const int q = A.pairs[k].y;
         if (q >= 0 && A.Q.len[q] > 0) {
           g = pair_geo_s(A, static_cast<int>(f), q, xs, n);
-          wq = static_cast<double>(A.wq[q]);
+          wq = A.wq[q];
         }
       }
       const int nq = static_cast<int>((q1 - qb < 32) ? (q1 - qb) : 32);
@@ -265,15 +305,24 @@ __global__ void __launch_bounds__(kXW * 32) xcf_kernel(XcfArgs A, int cap) {
         h.sP = __shfl_sync(kFull, g.sP, t);
         h.X0 = __shfl_sync(kFull, g.X0, t);
         h.Y0 = __shfl_sync(kFull, g.Y0, t);
-        const double wqt = __shfl_sync(kFull, wq, t);
+        const float wqt = __shfl_sync(kFull, wq, t);
         for (int base = i0; base < i1; base += 32) {
           const int j = base + lane;
-          const int bin = (j < i1) ? pixel_bin(h, xs[j], A.n_par, A.n_perp) : -1;
-          const int r0 = run_start(bin, lane);
-          if (r0 >= 0) {
-            const int j0 = base + r0;
-            atomicAdd(&snum[bin], wqt * (Pwd[j + 1] - Pwd[j0]));
-            atomicAdd(&sw[bin], wqt * (Pw[j + 1] - Pw[j0]));
+          int bin = -1;
+          float hn = 0.f, ln = 0.f, hw = 0.f, lw = 0.f;
+          if (j < i1) {
+            const Pix P = sp[j];
+            bin = pixel_bin(h, P.x, A.n_par, A.n_perp);
+            if (bin >= 0) {
+              hn = wqt * P.z;
+              ln = fmaf(wqt, P.z, -hn);
+              hw = wqt * P.y;
+              lw = fmaf(wqt, P.y, -hw);
+            }
+          }
+          if (run_scan(bin, lane, hn, ln, hw, lw)) {
+            df_atomic_add(reinterpret_cast<float2*>(&hist[bin]), hn, ln, A.err);
+            df_atomic_add(reinterpret_cast<float2*>(&hist[bin]) + 1, hw, lw, A.err);
           }
         }
       }
@@ -281,8 +330,11 @@ __global__ void __launch_bounds__(kXW * 32) xcf_kernel(XcfArgs A, int cap) {
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-    if (snum[k] != 0.0) red_add_f64_global(A.num + k, snum[k]);
-    if (sw[k] != 0.0) red_add_f64_global(A.wsum + k, sw[k]);
+    const float4 v = hist[k];
+    const double sn = static_cast<double>(v.x) + static_cast<double>(v.y);
+    const double sw = static_cast<double>(v.z) + static_cast<double>(v.w);
+    if (sn != 0.0) red_add_f64_global(A.num + k, sn);
+    if (sw != 0.0) red_add_f64_global(A.wsum + k, sw);
   }
 }
 
@@ -439,7 +491,7 @@ int grid_for(int64_t n, int threads) {
 
 int xcf_smem_bytes(int nb, int max_len) {
   const int cap = std::max(max_len, 1);
-  return 16 * nb + 16 * (cap + 1) + 4 * cap;
+  return 16 * nb + 20 * cap;
 }
 
 int xdm_warps(const DevInfo& dev, int max_len) {
@@ -453,9 +505,16 @@ int xi1d_smem_bytes(int n_bins, int max_len) {
   return 16 * n_bins + 16 * (cap + 1) + 12 * cap;
 }
 
-cudaError_t launch_qso_prep(const lya_quasars& q, Forests Q, unsigned* err, cudaStream_t s) {
+cudaError_t launch_qso_prep(const lya_quasars& q, Forests Q, unsigned* err, unsigned long long* fp,
+                            cudaStream_t s) {
   if (q.n <= 0) return cudaSuccess;
-  LYA_COUNT(1), qso_prep_kernel<<<grid_for(q.n, 256), 256, 0, s>>>(q, Q, err);
+  LYA_COUNT(1), qso_prep_kernel<<<grid_for(q.n, 256), 256, 0, s>>>(q, Q, err, fp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_own_hash(const int64_t* own, int64_t n, unsigned long long* fp, cudaStream_t s) {
+  if (!own || n <= 0) return cudaSuccess;
+  LYA_COUNT(1), own_hash_kernel<<<grid_for(n, 256), 256, 0, s>>>(own, n, fp);
   return cudaGetLastError();
 }
 
@@ -466,11 +525,11 @@ cudaError_t launch_xcf(const XcfArgs& a, const DevInfo& dev, cudaStream_t s) {
   cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(xcf_kernel), smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xcf_kernel, kXW * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xcf_kernel, kXCW * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(dev.sms) * per_sm, a.F.n));
-  LYA_COUNT(1), xcf_kernel<<<blocks, kXW * 32, smem, s>>>(a, cap);
+  LYA_COUNT(1), xcf_kernel<<<blocks, kXCW * 32, smem, s>>>(a, cap);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,31 @@ def test_xcf_own_quasar_excluded_or_not(api, handle, small):
     assert diff[: bins.n_par // 2, 0].sum() > 1e-6 * W2[: bins.n_par // 2, 0].sum()
 
 
+def test_pair_list_cache_follows_the_inputs(api, small):
+    """The (forest, quasar) list is reused only for the same pointers, sizes,
+    bins and geometry: in-place changes of the own-quasar indices or of the
+    quasar positions rebuild it."""
+    cat, q, own, bins, _ = small
+    dc, dq = api.DeviceCatalog.from_host(cat), api.DeviceQuasars.from_host(q)
+    own_d = torch.from_numpy(own).cuda()
+    h, fresh = api.Handle(), api.Handle()
+    try:
+        _, w_own, _ = api.lya_xcf(h, dc, dq, bins, forest_qso=own_d)
+        _, w_none, _ = api.lya_xcf(fresh, dc, dq, bins, forest_qso=None)
+        own_d.fill_(-1)                      # same tensor, no own quasar any more
+        _, w2, _ = api.lya_xcf(h, dc, dq, bins, forest_qso=own_d)
+        np.testing.assert_allclose(_np(w2), _np(w_none), rtol=1e-12, atol=1e-12)
+        assert not np.allclose(_np(w2), _np(w_own), rtol=1e-9, atol=0)
+        dq.ra.add_(2e-3)                     # move every quasar in place
+        _, w3, _ = api.lya_xcf(h, dc, dq, bins, forest_qso=own_d)
+        _, w4, _ = api.lya_xcf(fresh, dc, dq, bins, forest_qso=own_d)
+        np.testing.assert_allclose(_np(w3), _np(w4), rtol=1e-12, atol=1e-12)
+        assert not np.allclose(_np(w3), _np(w2), rtol=1e-9, atol=0)
+    finally:
+        h.close()
+        fresh.close()
+
+
 def test_xdmat_matches_oracle(api, handle, small):
     cat, q, own, bins, pl = small
     seed, p = 4321, 0.05
