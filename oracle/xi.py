@@ -111,3 +111,55 @@ def xi_sums(cat, bins, pair_list=None, delta=None, eps_edge: float = 0.0,
     out["sigma"] = np.divide(np.sqrt(out["num_sq"]), w, out=np.zeros_like(w), where=w != 0)
     out["pairs"] = len(a)
     return out
+
+
+def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0):
+    """Per-bin weighted means of the separations and of the pair distance, and
+    pixel-pair counts, over the pixel pairs of Eq. (2.4):
+
+        rpar_mean_A  = sum_A w_i w_j r_par / W_A,   rperp_mean_A = sum_A w_i w_j r_perp / W_A,
+        dist_mean_A  = sum_A w_i w_j (d_i + d_j) / 2 / W_A,   count_A = number of pairs in A,
+
+    0 where W_A = 0.  These are the per-bin columns a PICCA/Vega fit reads next
+    to xi (the paper exports its results for Vega, Appendix A); the redshift of
+    a bin follows from dist_mean through the caller's d(z).  With eps_edge > 0
+    also ``edge_c``, the number of pairs within eps of an edge per candidate
+    bin (as ``edge_w`` counts their weight)."""
+    if pair_list is None:
+        pair_list = _pairs.forest_pairs(cat, bins)
+    nb = bins.nbins
+    W, WP, WT, WD, cnt, ew, ec = (np.zeros(nb) for _ in range(7))
+    nvec = unit_vectors(cat.ra, cat.dec)
+    for a, b in zip(*pair_list):
+        sa, sb = cat.forest(a), cat.forest(b)
+        if sa.stop == sa.start or sb.stop == sb.start:
+            continue
+        c, s = half_angle(nvec[a], nvec[b])
+        r_par, r_perp = separations(cat.dist[sa], cat.dist[sb], c, s)
+        A, ok, x, y = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
+        tw = cat.weight[sa].astype(np.float64)[:, None] * cat.weight[sb].astype(np.float64)[None, :]
+        dm = 0.5 * (np.asarray(cat.dist[sa], dtype=np.float64)[:, None] + np.asarray(cat.dist[sb], dtype=np.float64)[None, :])
+        Ai = A[ok]
+        W += np.bincount(Ai, weights=tw[ok], minlength=nb)
+        WP += np.bincount(Ai, weights=(tw * r_par)[ok], minlength=nb)
+        WT += np.bincount(Ai, weights=(tw * r_perp)[ok], minlength=nb)
+        WD += np.bincount(Ai, weights=(tw * dm)[ok], minlength=nb)
+        cnt += np.bincount(Ai, minlength=nb)
+        if eps_edge > 0.0:
+            p_lo = np.floor(np.maximum(x - eps_edge, 0.0))
+            p_hi = np.floor(x + eps_edge)
+            t_lo = np.floor(np.maximum(y - eps_edge, 0.0))
+            t_hi = np.floor(y + eps_edge)
+            amb = (p_lo != p_hi) | (t_lo != t_hi)
+            if np.any(amb):
+                pl, ph, tl, th = p_lo[amb], p_hi[amb], t_lo[amb], t_hi[amb]
+                aw = np.abs(tw[amb])
+                for pp, tt, use in ((pl, tl, np.ones_like(pl, dtype=bool)), (ph, tl, ph != pl),
+                                    (pl, th, th != tl), (ph, th, (ph != pl) & (th != tl))):
+                    m = use & (pp < bins.n_par) & (tt < bins.n_perp)
+                    idx = (pp[m] * bins.n_perp + tt[m]).astype(np.int64)
+                    ew += np.bincount(idx, weights=aw[m], minlength=nb)
+                    ec += np.bincount(idx, minlength=nb)
+    div = lambda v: np.divide(v, W, out=np.zeros_like(W), where=W != 0)
+    return {"wsum": W, "rpar_mean": div(WP), "rperp_mean": div(WT), "dist_mean": div(WD), "count": cnt,
+            "edge_w": ew, "edge_c": ec}

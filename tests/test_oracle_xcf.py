@@ -259,3 +259,4 @@ def test_1d_equals_auto_of_two_copies():
     np.testing.assert_allclose(W0[:, 0], 2 * one["wsum"] + zero * np.sum(w * w), rtol=1e-13)
     np.testing.assert_allclose(N0[:, 0], 2 * one["num"] + zero * np.sum(wd * wd), rtol=1e-12, atol=1e-12)
     assert np.all(W0[:, 1:] == 0)
+
