@@ -726,7 +726,8 @@ def run_xcf(args, rank, world, local):
     r_par in [-200, 200) Mpc/h in 100 bins, r_perp < 200 in 50.  A step is the
     cross-correlation and its distortion matrix (2% of the forest-quasar pairs)
     on the cached (forest, quasar) list, whose build is timed once beside it;
-    the 1D same-forest correlation (50 bins to 200 Mpc/h) is timed on its own."""
+    the 1D same-forest correlation (50 bins to 200 Mpc/h) and the per-bin
+    means and counts of the auto-correlation are timed on their own."""
     import time
     import torch
     from paper_2507_00129_gb300 import synth, build
@@ -787,9 +788,22 @@ def run_xcf(args, rank, world, local):
             api.lya_xi1d(h, dc, 50, 200.0)
         f1.record()
         torch.cuda.synchronize()
+    # per-bin means and counts of the auto-correlation (50 x 50 bins to 200), on its cached pair list
+    abins = synth.bins_for(1)
+    bm = api.lya_xi_bin_means(h, dc, abins)
+    torch.cuda.synchronize()
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record()
+    for _ in range(args.steps):
+        bm = api.lya_xi_bin_means(h, dc, abins)
+    m1.record()
+    torch.cuda.synchronize()
     api.lya_sync_status(h)
     ms_local = e0.elapsed_time(e1) / args.steps
     ms1d = f0.elapsed_time(f1) / args.steps
+    ms_means = m0.elapsed_time(m1) / args.steps
+    n_means = float(bm["count"].sum())
     ms, tot, value = aggregate(ms_local, pix_pairs, world)
     line = {
         "metric": "forest-quasar pixel pairs/s (cross-correlation + its D)", "value": value,
@@ -805,6 +819,8 @@ def run_xcf(args, rank, world, local):
         "pair_build_ms": pair_build_ms,
         "xi1d": {"ms": ms1d, "pixel_pairs": pix_pairs_1d, "pairs_per_s": pix_pairs_1d / (ms1d * 1e-3),
                  "bins": 50, "r_max": 200.0},
+        "bin_means": {"ms": ms_means, "pixel_pairs": n_means, "pairs_per_s": n_means / (ms_means * 1e-3),
+                      "bins": [abins.n_par, abins.n_perp]},
         "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:

@@ -269,6 +269,22 @@ typedef struct {
 int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double* num, double* wsum,
             double* xi, void* stream);
 
+/* Per-bin weighted means of the separations and of the pair distance, and
+ * pixel-pair counts, over the pixel pairs of Eq. (2.4) (the per-bin columns a
+ * PICCA/Vega fit reads next to xi; the paper exports its results for Vega,
+ * Appendix A):
+ *   rpar_mean[A]  = sum_A w_i w_j r_par / W_A,   rperp_mean[A] = sum_A w_i w_j r_perp / W_A,
+ *   dist_mean[A]  = sum_A w_i w_j (d_i + d_j)/2 / W_A  (Mpc/h; the bin's redshift
+ *                   follows from the caller's d(z)),   npairs[A] = pixel pairs in A,
+ * 0 where W_A = 0; wsum (optional) receives W_A.  Each [n_par*n_perp]
+ * (float64; npairs int64).  Same pair list and FP32 bin arithmetic as the
+ * mixed path of lya_xi; run sums in FP32, accumulation in double-float then
+ * FP64.  Builds the pair list if none is cached (synchronises); refused
+ * during graph capture.  Limit: 36 bytes per bin + 8 per pixel of the longest
+ * forest of shared memory. */
+int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double* wsum, double* rpar_mean,
+                     double* rperp_mean, double* dist_mean, int64_t* npairs, void* stream);
+
 /* Point tracers (quasars) for the forest x quasar cross-correlation.  Entries
  * with a non-finite or non-positive distance, non-finite position or weight,
  * or a negative weight are skipped and flagged (LYA_ERR_NONFINITE at the

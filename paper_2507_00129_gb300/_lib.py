@@ -80,6 +80,7 @@ SIGNATURES = {
     "lya_xi_subsamples": (c_int, [H, CAT, BINS, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xi_covariance": (c_int, [H, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "lya_xi3": (c_int, [H, CAT, BINS3, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lya_xi_bin_means": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xcf": (c_int, [H, CAT, QSO, c_void_p, BINS, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xdmat": (c_int, [H, CAT, QSO, c_void_p, BINS, c_int, c_double, c_uint64, c_void_p, c_void_p,
                           c_void_p]),

@@ -303,6 +303,20 @@ def lya_xi3(handle: Handle, cat: DeviceCatalog, grid, stream=None):
     return num, wsum, xi
 
 
+def lya_xi_bin_means(handle: Handle, cat: DeviceCatalog, bins, stream=None):
+    """Per-bin weighted mean r_par, r_perp and pair distance, W and pixel-pair
+    counts: dict of [n_par n_perp] tensors."""
+    nb = bins.n_par * bins.n_perp
+    out = {k: torch.empty(nb, dtype=torch.float64, device="cuda")
+           for k in ("wsum", "rpar_mean", "rperp_mean", "dist_mean")}
+    out["count"] = torch.empty(nb, dtype=torch.int64, device="cuda")
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_bin_means(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(out["wsum"]),
+                                                 _ptr(out["rpar_mean"]), _ptr(out["rperp_mean"]),
+                                                 _ptr(out["dist_mean"]), _ptr(out["count"]), _stream(stream)))
+    return out
+
+
 class DeviceQuasars:
     """Quasars resident on the GPU (layout of ``lya_quasars``)."""
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblya.so")
-SOURCES = ["api.cu", "prep.cu", "pairs.cu", "xi.cu", "dmat.cu", "adjoint.cu", "noalloc.cu", "cov.cu", "xi3.cu", "xcf.cu"]
+SOURCES = ["api.cu", "prep.cu", "pairs.cu", "xi.cu", "dmat.cu", "adjoint.cu", "noalloc.cu", "cov.cu", "xi3.cu", "xcf.cu", "means.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1020,6 +1020,40 @@ int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double
   return LYA_OK;
 }
 
+int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double* wsum, double* rpar_mean,
+                     double* rperp_mean, double* dist_mean, int64_t* npairs, void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!rpar_mean || !rperp_mean || !dist_mean || !npairs)
+    return fail(h, LYA_ERR_INVALID_ARG, "rpar_mean, rperp_mean, dist_mean and npairs are required");
+  if ((st = refuse_in_capture(h, "lya_xi_bin_means"))) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = prepare(h, cat, 1, s))) return st;
+  if ((st = ensure_pairs(h, cat, 1, bins, s))) return st;
+  const int nb = bins->n_par * bins->n_perp;
+  if (means_smem_bytes(nb, h->max_len) > h->dev.smem_optin)
+    return fail(h, LYA_ERR_TOO_LARGE, "bin means: 36 bytes per bin + 8 per pixel of the longest forest above shared memory");
+  cudaError_t e = grow(&h->scratch2, &h->scratch2_cap, means_scratch_bytes(h->F.n, h->n_pairs, nb));
+  if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "bin-means scratch");
+  MeansArgs A{};
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  A.d_par = bins->r_par_max / bins->n_par;
+  A.d_perp = bins->r_perp_max / bins->n_perp;
+  A.err = h->d_err;
+  A.max_len = h->max_len;
+  stage_begin(h, 0, s);
+  CK(launch_bin_means(A, h->dev, h->scratch2, wsum, rpar_mean, rperp_mean, dist_mean, npairs, s), "bin means");
+  stage_end(h, 0, s);
+  return LYA_OK;
+}
+
 // ---------------------------------------------------------------------------
 // forest x quasar cross-correlation, its distortion matrix, 1D correlation
 // ---------------------------------------------------------------------------

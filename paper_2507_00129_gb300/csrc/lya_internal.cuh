@@ -303,6 +303,28 @@ struct X1Args {
 int xi1d_smem_bytes(int n_bins, int max_len);
 cudaError_t launch_xi1d(const X1Args& a, const Pix* pix, const DevInfo& dev, cudaStream_t s);
 
+// pairs.cu: out[k] = sum_{j<k} in[j] for k <= n (one block; n up to a few million)
+cudaError_t launch_exclusive_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+
+// means.cu: per-bin weighted means of r_par, r_perp and the pair distance, and
+// pixel-pair counts, over the cached forest-pair list
+struct MeansArgs {
+  const int2* pairs;     // (a < b)
+  const float2* cs;      // (cos(theta/2)/D_par, sin(theta/2)/D_perp) per pair
+  int64_t n_pairs;
+  const Pix* pix;
+  Forests F;
+  int n_par, n_perp;
+  double d_par, d_perp;  // bin widths
+  unsigned* err;
+  int max_len;
+};
+size_t means_scratch_bytes(int64_t n_forests, int64_t n_pairs, int nb);
+int means_smem_bytes(int nb, int max_len);
+// outputs: wsum, rpar_mean, rperp_mean, dist_mean [nb] float64 (wsum may be NULL), count [nb] int64
+cudaError_t launch_bin_means(const MeansArgs& a, const DevInfo& dev, void* scratch, double* wsum, double* rpar_mean,
+                             double* rperp_mean, double* dist_mean, int64_t* count, cudaStream_t s);
+
 // scratch helper (api.cu).  While the calling thread captures a CUDA graph
 // (lya_capture_begin) it allocates nothing and fails with
 // cudaErrorNotPermitted if the buffer is too small.

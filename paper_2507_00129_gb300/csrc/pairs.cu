@@ -796,3 +796,12 @@ cudaError_t build_cross_pairs(const Forests& F, const Forests& Q, int nside, dou
 }
 
 }  // namespace lya
+
+namespace lya {
+
+cudaError_t launch_exclusive_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s) {
+  LYA_COUNT(1), scan_kernel<<<1, 1024, 0, s>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lya
