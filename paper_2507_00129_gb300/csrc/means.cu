@@ -15,39 +15,13 @@
 
 #include <algorithm>
 
-#include "lya_internal.cuh"
+#include "dfloat.cuh"
 
 namespace lya {
 namespace {
 
 constexpr int kMW = 16;   // warps per block
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRetry = 1 << 16;
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (hi, lo) float pair at p += h + l; bounded compare-and-swap (FLAG_RETRY on give-up)
-__device__ __forceinline__ void df_add(float2* p, float h, float l, unsigned* err) {
-  unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
-  unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
-  for (int it = 0; it < kRetry; ++it) {
-    float s, e;
-    two_sum(__uint_as_float(static_cast<unsigned>(old)), h, s, e);
-    const float t = __uint_as_float(static_cast<unsigned>(old >> 32)) + l + e;
-    const float H = s + t;
-    const float L = t - (H - s);
-    const unsigned long long nw = static_cast<unsigned long long>(__float_as_uint(H)) |
-                                  (static_cast<unsigned long long>(__float_as_uint(L)) << 32);
-    const unsigned long long seen = atomicCAS(a, old, nw);
-    if (seen == old) return;
-    old = seen;
-  }
-  atomicOr(err, FLAG_RETRY);
-}
 
 __device__ __forceinline__ int below(const float* a, int n, float v) {
   int lo = 0, hi = n;
@@ -200,10 +174,10 @@ __global__ void __launch_bounds__(kMW * 32, 2) means_kernel(MeansArgs A, const i
               }
               const int r0 = run_sums(bin, lane, v0, v1, v2, v3);
               if (r0 >= 0) {
-                df_add(reinterpret_cast<float2*>(&h1[bin]), v0, 0.f, A.err);
-                df_add(reinterpret_cast<float2*>(&h1[bin]) + 1, v1, 0.f, A.err);
-                df_add(reinterpret_cast<float2*>(&h2[bin]), v2, 0.f, A.err);
-                df_add(reinterpret_cast<float2*>(&h2[bin]) + 1, 0.5f * fmaf(St, v0, v3), 0.f, A.err);
+                df_atomic_add(reinterpret_cast<float2*>(&h1[bin]), v0, 0.f, A.err);
+                df_atomic_add(reinterpret_cast<float2*>(&h1[bin]) + 1, v1, 0.f, A.err);
+                df_atomic_add(reinterpret_cast<float2*>(&h2[bin]), v2, 0.f, A.err);
+                df_atomic_add(reinterpret_cast<float2*>(&h2[bin]) + 1, 0.5f * fmaf(St, v0, v3), 0.f, A.err);
                 atomicAdd(&hc[bin], static_cast<unsigned>(lane - r0 + 1));
               }
             }

@@ -34,7 +34,7 @@
 
 #include <algorithm>
 
-#include "lya_internal.cuh"
+#include "dfloat.cuh"
 
 namespace lya {
 namespace {
@@ -42,12 +42,6 @@ namespace {
 constexpr int kXW = 8;    // warps per block (distortion matrix)
 constexpr int kXCW = 16;  // warps per block of the cross-correlation (two blocks per SM share the shared memory)
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 
 // FP32 bin coordinates of a (forest, quasar) pair:
 //   x = (r_par + r_par_max) / D_par = fma(x_i, cP, X0),  y = r_perp / D_perp = fma(x_i, sP, Y0)
@@ -231,32 +225,6 @@ __device__ __forceinline__ int run_start(int bin, int lane) {
   const unsigned hm = __ballot_sync(kFull, head);
   if (!tail) return -1;
   return 31 - __clz(hm & (0xffffffffu >> (31 - lane)));
-}
-
-// Add the double-float value (h, l) to the double-float pair at p (hi, lo as
-// one 64-bit word) by compare-and-swap; TwoSum keeps the rounding error of the
-// high part in the low part.  Gives up (and flags) after kRetry failed swaps,
-// each of which means another thread's update went through.
-constexpr int kRetry = 1 << 16;
-
-__device__ __forceinline__ void df_atomic_add(float2* p, float h, float l, unsigned* err) {
-  unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
-  unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a);
-  for (int it = 0; it < kRetry; ++it) {
-    const float2 cur = make_float2(__uint_as_float(static_cast<unsigned>(old)),
-                                   __uint_as_float(static_cast<unsigned>(old >> 32)));
-    float s, e;
-    two_sum(cur.x, h, s, e);
-    const float t = cur.y + l + e;
-    const float H = s + t;
-    const float L = t - (H - s);
-    const unsigned long long nw = static_cast<unsigned long long>(__float_as_uint(H)) |
-                                  (static_cast<unsigned long long>(__float_as_uint(L)) << 32);
-    const unsigned long long seen = atomicCAS(a, old, nw);
-    if (seen == old) return;
-    old = seen;
-  }
-  atomicOr(err, FLAG_RETRY);
 }
 
 // One block per forest (grid-stride): the forest's packed pixels are staged in
