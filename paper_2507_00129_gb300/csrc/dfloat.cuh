@@ -39,4 +39,10 @@ __device__ __forceinline__ void df_atomic_add(float2* p, float h, float l, unsig
   atomicOr(err, FLAG_RETRY);
 }
 
+// Barrier among the `threads` threads of one team of a block (named barrier
+// `id` >= 1; id 0 is __syncthreads).
+__device__ __forceinline__ void team_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 }  // namespace lya

@@ -91,35 +91,41 @@ __device__ __forceinline__ int run_sums(int bin, int lane, float& v0, float& v1,
 // length to the count histogram.
 __global__ void __launch_bounds__(kMW * 32, 2) means_kernel(MeansArgs A, const int64_t* poff, const int32_t* plist,
                                                              Acc acc) {
-  extern __shared__ float4 msh[];   // h1[nb] = (W, WX) | h2[nb] = (WY, WD) | hc[nb] u32 | xa[cap] | wa[cap]
+  // h1[nb] = (W, WX) | h2[nb] = (WY, WD) | hc[nb] u32 | per team: xa[cap], wa[cap]
+  extern __shared__ float4 msh[];
   const int nb = A.n_par * A.n_perp;
   const int cap = A.max_len;
   float4* h1 = msh;
   float4* h2 = msh + nb;
   unsigned* hc = reinterpret_cast<unsigned*>(msh + 2 * nb);
-  float* xa = reinterpret_cast<float*>(hc + nb);
-  float* wa = xa + cap;
   for (int k = threadIdx.x; k < nb; k += blockDim.x) {
     h1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     h2[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     hc[k] = 0u;
   }
+  __syncthreads();
+  // two teams of kMW / 2 warps on their own first forests (own staging and
+  // barrier), adding to the block's histograms
+  constexpr int kTeamWarps = kMW / 2;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int team = wi / kTeamWarps, tw = wi % kTeamWarps, tt = threadIdx.x % (kTeamWarps * 32);
+  float* xa = reinterpret_cast<float*>(hc + nb) + static_cast<size_t>(team) * 2 * cap;
+  float* wa = xa + cap;
   const float fnpar = static_cast<float>(A.n_par), fnperp = static_cast<float>(A.n_perp);
-  for (int64_t f = blockIdx.x; f < A.F.n; f += gridDim.x) {
+  for (int64_t f = 2 * static_cast<int64_t>(blockIdx.x) + team; f < A.F.n; f += 2 * static_cast<int64_t>(gridDim.x)) {
     const int64_t k0 = poff[f], k1 = poff[f + 1];
     const int n = A.F.len[f];
-    if (k1 <= k0 || n <= 0 || n > cap) continue;   // uniform over the block
-    __syncthreads();
+    if (k1 <= k0 || n <= 0 || n > cap) continue;   // uniform over the team
+    team_sync(1 + team, kTeamWarps * 32);
     const Pix* pa = A.pix + A.F.off[f];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = tt; k < n; k += kTeamWarps * 32) {
       const Pix P = pa[k];
       xa[k] = P.x;
       wa[k] = P.y;
     }
-    __syncthreads();
+    team_sync(1 + team, kTeamWarps * 32);
     const float dref_a = A.F.dref[f];
-    for (int64_t kk = k0 + wi; kk < k1; kk += kMW) {
+    for (int64_t kk = k0 + tw; kk < k1; kk += kTeamWarps) {
       const int k = plist[kk];
       const int b = A.pairs[k].y;
       if (b < 0) continue;
@@ -229,7 +235,7 @@ size_t means_scratch_bytes(int64_t n_forests, int64_t n_pairs, int nb) {
          al256(std::max<int64_t>(n_pairs, 1) * 4);
 }
 
-int means_smem_bytes(int nb, int max_len) { return 36 * nb + 8 * std::max(max_len, 1); }
+int means_smem_bytes(int nb, int max_len) { return 36 * nb + 2 * 8 * std::max(max_len, 1); }
 
 cudaError_t launch_bin_means(const MeansArgs& a, const DevInfo& dev, void* scratch, double* wsum, double* rpar_mean,
                              double* rperp_mean, double* dist_mean, int64_t* count, cudaStream_t s) {
@@ -264,7 +270,7 @@ cudaError_t launch_bin_means(const MeansArgs& a, const DevInfo& dev, void* scrat
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, means_kernel, kMW * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(dev.sms) * per_sm, a.F.n));
+    const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(dev.sms) * per_sm, (a.F.n + 1) / 2));
     LYA_COUNT(1), means_kernel<<<blocks, kMW * 32, smem, s>>>(a, poff, plist, acc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

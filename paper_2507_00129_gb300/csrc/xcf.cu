@@ -234,26 +234,34 @@ __device__ __forceinline__ int run_start(int bin, int lane) {
 // a segmented TwoSum scan forms each run's sum, and the run's last lane adds
 // it to the block's double-float histogram: no FP64 arithmetic per pixel.
 __global__ void __launch_bounds__(kXCW * 32, 2) xcf_kernel(XcfArgs A, int cap) {
-  extern __shared__ float4 xs4[];   // [nb] (num hi, num lo, w hi, w lo) | staged pixels [cap] | xs [cap]
+  // [nb] (num hi, num lo, w hi, w lo) | per team: staged pixels [cap], xs [cap]
+  extern __shared__ float4 xs4[];
   const int nb = A.n_par * A.n_perp;
   float4* hist = xs4;
-  Pix* sp = xs4 + nb;
-  float* xs = reinterpret_cast<float*>(sp + cap);
   for (int k = threadIdx.x; k < nb; k += blockDim.x) hist[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  // two teams of kXCW / 2 warps, each on its own forests with its own staging
+  // buffer and barrier, so that one team's wait for its slowest warp leaves
+  // the other team issuing; both add to the block's histogram
+  constexpr int kTeamWarps = kXCW / 2;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  for (int64_t f = blockIdx.x; f < A.F.n; f += gridDim.x) {
+  const int team = wi / kTeamWarps, tw = wi % kTeamWarps, tt = threadIdx.x % (kTeamWarps * 32);
+  Pix* sp = reinterpret_cast<Pix*>(xs4 + nb) + static_cast<size_t>(team) * cap;
+  float* xs = reinterpret_cast<float*>(reinterpret_cast<Pix*>(xs4 + nb) + 2 * static_cast<size_t>(cap)) +
+              static_cast<size_t>(team) * cap;
+  for (int64_t f = 2 * static_cast<int64_t>(blockIdx.x) + team; f < A.F.n; f += 2 * static_cast<int64_t>(gridDim.x)) {
     const int64_t q0 = A.qoff[f], q1 = A.qoff[f + 1];
     const int n = A.F.len[f];
-    if (q1 <= q0 || n <= 0 || n > cap) continue;   // uniform over the block
-    __syncthreads();                               // the previous forest's readers are done
+    if (q1 <= q0 || n <= 0 || n > cap) continue;   // uniform over the team
+    team_sync(1 + team, kTeamWarps * 32);          // the team's previous forest's readers are done
     const Pix* fp = A.pix + A.F.off[f];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int k = tt; k < n; k += kTeamWarps * 32) {
       const Pix P = fp[k];
       sp[k] = P;
       xs[k] = P.x;
     }
-    __syncthreads();
-    for (int64_t qb = q0 + static_cast<int64_t>(wi) * 32; qb < q1; qb += kXCW * 32) {
+    team_sync(1 + team, kTeamWarps * 32);
+    for (int64_t qb = q0 + static_cast<int64_t>(tw) * 32; qb < q1; qb += kTeamWarps * 32) {
       XGeo g{0.f, 0.f, 0.f, 0.f, 0, 0};
       float wq = 0.f;
       const int64_t k = qb + lane;
@@ -459,7 +467,7 @@ int grid_for(int64_t n, int threads) {
 
 int xcf_smem_bytes(int nb, int max_len) {
   const int cap = std::max(max_len, 1);
-  return 16 * nb + 20 * cap;
+  return 16 * nb + 2 * 20 * cap;
 }
 
 int xdm_warps(const DevInfo& dev, int max_len) {
@@ -496,7 +504,7 @@ cudaError_t launch_xcf(const XcfArgs& a, const DevInfo& dev, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xcf_kernel, kXCW * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(dev.sms) * per_sm, a.F.n));
+  const int blocks = static_cast<int>(std::min<int64_t>(static_cast<int64_t>(dev.sms) * per_sm, (a.F.n + 1) / 2));
   LYA_COUNT(1), xcf_kernel<<<blocks, kXCW * 32, smem, s>>>(a, cap);
   return cudaGetLastError();
 }
