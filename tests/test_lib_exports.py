@@ -50,6 +50,12 @@ def test_null_handle_is_rejected_on_host(lib):
     assert lib.lya_xi(None, None, None, 1, None, None, None, None) == -1
     assert lib.lya_destroy(None) == -1
     assert lib.lya_last_error(None, None, 0) == -1
+    # the extension entry points check the handle before touching the device
+    assert lib.lya_xcf(None, None, None, None, None, None, None, None, None) == -1
+    assert lib.lya_xdmat(None, None, None, None, None, 1, 1.0, 0, None, None, None) == -1
+    assert lib.lya_xi1d(None, None, 10, 50.0, None, None, None, None) == -1
+    assert lib.lya_xi_bin_means(None, None, None, None, None, None, None, None, None) == -1
+    assert lib.lya_xi3(None, None, None, None, None, None, None) == -1
 
 
 def test_api_fails_loudly_without_library(tmp_path, monkeypatch):
