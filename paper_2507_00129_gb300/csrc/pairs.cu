@@ -404,17 +404,20 @@ __global__ void cross_cell_pair_kernel(const CellStat* sf, int64_t KF, const Cel
 
 // Forest a and quasar q can hold an in-grid pixel: r_perp >= (d_first + d_q) sin(theta/2) and
 // |r_par| >= (distance from d_q to the forest's distance range) cos(theta/2), both exact bounds.
+// Compared as squares (all terms are non-negative): sin^2(theta/2) = |n_a - n_q|^2 / 4 and
+// cos^2(theta/2) = |n_a + n_q|^2 / 4, so no square root is taken (FP64 is slow on this part).
 __device__ __forceinline__ bool forest_quasar_pair(const Forests& F, int32_t a, const Forests& Q, int32_t q,
                                                    double rpar_max, double rperp_max) {
   const double ax = F.ux[a], ay = F.uy[a], az = F.uz[a];
   const double qx = Q.ux[q], qy = Q.uy[q], qz = Q.uz[q];
   const double dx = ax - qx, dy = ay - qy, dz = az - qz;
   const double sx = ax + qx, sy = ay + qy, sz = az + qz;
-  const double s = 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
-  const double c = 0.5 * sqrt(sx * sx + sy * sy + sz * sz);
-  if ((F.dmin[a] + Q.dmin[q]) * s >= rperp_max) return false;
+  const double s2 = 0.25 * (dx * dx + dy * dy + dz * dz);
+  const double c2 = 0.25 * (sx * sx + sy * sy + sz * sz);
+  const double dsum = F.dmin[a] + Q.dmin[q];
+  if (dsum * dsum * s2 >= rperp_max * rperp_max) return false;
   const double gap = fmax(0.0, fmax(Q.dmin[q] - F.dmax[a], F.dmin[a] - Q.dmin[q]));
-  return gap * c < rpar_max;
+  return gap * gap * c2 < rpar_max * rpar_max;
 }
 
 // one warp per (forest cell, quasar cell) pair; MODE 0 counts, MODE 1 fills (forest, quasar)
