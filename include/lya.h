@@ -49,7 +49,7 @@ enum {
   LYA_ERR_NONFINITE = -3,     /* NaN/Inf input, or a negative weight */
   LYA_ERR_NO_MEMORY = -4,     /* device allocation failed */
   LYA_ERR_CUDA = -5,          /* a CUDA runtime call failed */
-  LYA_ERR_TIMEOUT = -6,       /* reserved: a bounded device wait gave up */
+  LYA_ERR_TIMEOUT = -6,       /* a bounded device retry loop gave up (shared-memory compare-and-swap) */
   LYA_ERR_DEVICE_CHECK = -7,  /* inconsistent offsets seen on the device */
   LYA_ERR_TOO_LARGE = -8      /* size beyond a documented limit */
 };
