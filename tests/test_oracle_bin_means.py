@@ -66,3 +66,28 @@ def test_bin_means_analytic_uniform_grid():
         exp = sum(k * m * h * c for k, m in zip(mult, ms)) / sum(mult)
         assert out["rpar_mean"][p * 2] == pytest.approx(exp, rel=1e-12)
         assert out["count"][p * 2] == sum(mult)
+
+
+def test_bin_means_edge_counts_bound_rebinning():
+    """Rescaling all distances by a factor that moves separations by less than
+    eps bin widths changes a bin's count by at most edge_c and its W by at
+    most edge_w."""
+    from conftest import random_small
+    cat = random_small(n_forests=8, max_len=8, patch_deg=0.6, seed=61, spread=30.0)
+    bins = synth.Bins(6, 4, 24.0, 24.0)
+    from oracle import pairs as opairs
+    pl = opairs.all_pairs(cat.n_forests)
+    eps = 0.02
+    ref = oxi.bin_means(cat, bins, pl, eps_edge=eps)
+    changed = False
+    # every separation scales by f: |f - 1| r <= 3e-3 x 24 Mpc/h = 0.072 Mpc/h, below eps = 0.02 bin widths
+    # (0.08 Mpc/h for r_par, 0.12 for r_perp)
+    for f in (1 + 3e-3, 1 - 3e-3):
+        moved = synth.Catalog(ra=cat.ra, dec=cat.dec, offsets=cat.offsets, dist=cat.dist * f,
+                              loglam=cat.loglam, delta=cat.delta, weight=cat.weight)
+        alt = oxi.bin_means(moved, bins, pl)
+        assert np.all(np.abs(alt["count"] - ref["count"]) <= ref["edge_c"])
+        assert np.all(np.abs(alt["wsum"] - ref["wsum"]) <= ref["edge_w"] + 1e-12)
+        changed |= bool(np.any(alt["count"] != ref["count"]))
+    assert ref["count"].sum() > 50
+    assert changed or ref["edge_c"].sum() == 0

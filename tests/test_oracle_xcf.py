@@ -260,3 +260,22 @@ def test_1d_equals_auto_of_two_copies():
     np.testing.assert_allclose(N0[:, 0], 2 * one["num"] + zero * np.sum(wd * wd), rtol=1e-12, atol=1e-12)
     assert np.all(W0[:, 1:] == 0)
 
+
+
+def test_xcf_edge_masses_bound_rebinning():
+    """Shifting every pixel distance by +-0.4 eps bin widths moves only pixels
+    within eps of an edge: |dW| <= edge_w and |dN| <= edge_n per bin."""
+    cat, q, bins = _dm_case(seed=51, r_max=24.0)
+    pl = ox.forest_quasar_pairs(cat, q, bins)
+    eps = 0.02
+    ref = ox.xcf_sums(cat, q, bins, pl, eps_edge=eps)
+    moved_any = False
+    for shift in (+0.4, -0.4):
+        moved = synth.Catalog(ra=cat.ra, dec=cat.dec, offsets=cat.offsets,
+                              dist=cat.dist + shift * eps * (2 * bins.r_par_max / bins.n_par),
+                              loglam=cat.loglam, delta=cat.delta, weight=cat.weight)
+        alt = ox.xcf_sums(moved, q, bins, pl)
+        assert np.all(np.abs(alt["wsum"] - ref["wsum"]) <= ref["edge_w"] + 1e-12)
+        assert np.all(np.abs(alt["num"] - ref["num"]) <= ref["edge_n"] + 1e-12)
+        moved_any |= bool(np.any(alt["count"] != ref["count"]))
+    assert moved_any and ref["edge_w"].sum() > 0
