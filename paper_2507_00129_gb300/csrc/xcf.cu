@@ -7,29 +7,34 @@
 // pixel of Eq. (2.4) with delta = 1:
 //     N_A = sum_{(i,q) in A} (w delta)_i w_q,   W_A = sum_{(i,q) in A} w_i w_q,
 // r_par = (d_i - d_q) cos(theta/2) signed and binned over [-r_par_max, r_par_max),
-// r_perp = (d_i + d_q) sin(theta/2).  One warp takes one (forest, quasar) pair:
-// the pixels that can land in the grid form one contiguous window of the
-// forest (binary search on the packed distances), each lane bins one pixel in
-// FP32 as x = fma(x_i, c/D_par, X0), y = fma(x_i, s/D_perp, Y0) with X0, Y0
-// formed in FP64, and because both grow with the pixel distance the bin index
-// never decreases along the window.  Equal bins therefore sit in adjacent
-// lanes: a segmented warp scan sums each run exactly (error-free FP32 products
-// w_q w_i and w_q (w delta)_i, TwoSum-compensated additions, i.e. about FP64
-// accuracy) and the last lane of a run adds it to the block's FP64 histogram
-// in shared memory, flushed to the global sums once per block.
+// r_perp = (d_i + d_q) sin(theta/2).  The (forest, quasar) list is grouped by
+// forest; a block holds two teams of warps, each staging one forest's packed
+// pixels in shared memory.  A warp takes 32 of the forest's quasars, one
+// pair's geometry per lane (FP64, then the window of pixels that can land in
+// the grid by binary search in shared memory), and walks each window with all
+// lanes: a lane bins one pixel in FP32 as x = fma(x_i, c/D_par, X0),
+// y = fma(x_i, s/D_perp, Y0) (X0, Y0 formed in FP64).  Both grow with the pixel
+// distance, so the bin never decreases along the window and equal bins sit in
+// adjacent lanes: a segmented warp scan sums each run (error-free FP32
+// products w_q w_i and w_q (w delta)_i, TwoSum-compensated additions) and the
+// run's last lane adds it to the block's double-float histogram (bounded
+// compare-and-swap), flushed to the FP64 sums once per block.
 //
 // Distortion matrix.  With eta = I - 1 u^T - x v^T the pair (a, q) adds
 // w_q (diag(alpha) - alpha alpha^T / W_a - beta beta^T / S_a) on the bins its
 // window touches, alpha[B] = sum_{k in B} w_k, beta[B] = sum_{k in B} w_k x_k.
-// The same segmented scan yields (bin, alpha, beta) per run; a warp keeps the
-// pair's run list in shared memory and adds the upper triangle (bins ascend
-// along the list) to D~ with FP64 global reductions; D = D~ / W_A row by row.
+// One warp per kept pair: the same segmented scan yields (bin, alpha, beta)
+// per run, kept as the pair's run list in shared memory; the warp adds the
+// upper triangle (bins ascend along the list) to D~ with FP64 global
+// reductions; D = D~ / W_A row by row.
 //
-// 1D correlation.  One block per forest stages the forest's FP64 distances,
-// weights and w delta in shared memory; thread i walks j > i while
-// floor((d_j - d_i) / D) < n_bins (the same FP64 division as the definition, so
-// every bin decision is exact) and adds each run of equal bins once to the
-// block's FP64 histogram.
+// 1D correlation.  One block per forest stages the forest's packed and FP64
+// distances and FP64 prefix sums of w and w delta; a warp takes one pixel i,
+// its lanes the pixels j > i.  The bin floor((d_j - d_i) / D) is taken from
+// FP32 values unless they lie within a guard band of an edge, where the FP64
+// division of the definition decides, so every bin decision is the
+// definition's; each run of equal bins adds (w delta)_i (P[j1+1] - P[j0]) to
+// the block's FP64 histogram.
 #include <math.h>
 
 #include <algorithm>
