@@ -43,6 +43,11 @@ FLOPS_PER_PAIR = 8  # 4 for the two scaled separations, 2 products, 2 accumulati
 XI_TRAFFIC = {"sha256": "48247fa6ec1db0575ee3697ff32bbfcf032d47d4aa87439259e8dc94e202a2b7", "bytes": 9421886208 + 13905152}
 
 
+# FP64 fused multiply-adds per SM per clock measured on this GB300 (a DFMA throughput
+# microbenchmark at 1.9 GHz); the plain-FP64 path's roofline uses it.
+FP64_DFMA_PER_SM_CLK = 1.7
+
+
 def xi_source_hash() -> str:
     import hashlib
     hsh = hashlib.sha256()
@@ -338,6 +343,15 @@ def run_ours(args, rank, world, local):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
     ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
+    if fp64 is not None:
+        # the plain-FP64 path against an FP64 peak from the DFMA rate measured on this part
+        # (1.7 DFMA per SM per clock in a microbenchmark), same 8 algorithmic flops per pair
+        peak_fp64 = n_sm * FP64_DFMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+        a64 = FLOPS_PER_PAIR * fp64["pixel_pairs_per_s"] / 1e12
+        fp64["roofline"] = {"bound": "fp64", "achieved": a64, "peak": peak_fp64, "unit": "TFLOP/s",
+                            "frac": a64 / peak_fp64,
+                            "peak_note": f"{n_sm} SMs x {FP64_DFMA_PER_SM_CLK} DFMA x 2 flops x {sm_max:.0f} MHz "
+                                         "(DFMA rate measured on this GB300)"}
     dominant = max(med, key=med.get)
     # FP32-vs-FP64 bin-edge flips of the mixed path on a seeded 1% of the forest pairs
     flips = api.lya_flip_tally(h, dcp, bins, 0.01, 99)
