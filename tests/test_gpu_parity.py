@@ -1,6 +1,7 @@
 """CUDA path (through the C ABI) against the CPU FP64 oracle.
 
-Tolerances (derived in the design doc):
+Tolerances (from the workload's 1e-6 / 1e-5 bars and the FP32 error bound of
+the mixed path's scaled separations):
 * FP64 path: |dW_A| <= 1e-6 W_A, |dxi_A| <= 1e-5 max(|xi_A|, sigma_A).
 * Mixed path: the same plus the oracle's edge mass for eps = 6e-5 bin units,
   the bound on the FP32 error of the scaled separations.
