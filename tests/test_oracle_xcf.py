@@ -279,3 +279,23 @@ def test_xcf_edge_masses_bound_rebinning():
         assert np.all(np.abs(alt["num"] - ref["num"]) <= ref["edge_n"] + 1e-12)
         moved_any |= bool(np.any(alt["count"] != ref["count"]))
     assert moved_any and ref["edge_w"].sum() > 0
+
+
+def test_pair_prefilter_drops_nothing():
+    """The (forest, quasar) prefilter keeps every pair with an in-grid or
+    edge-ambiguous pixel: sums over all pairs equal sums over the kept ones."""
+    spec = synth.Spec(n_forests=40, seed=9, region="box", box_deg=1.5, grid="log10")
+    cat = synth.generate(spec)
+    q, own = synth.quasars(spec, cat, extra_fraction=0.5)
+    bins = synth.Bins(20, 10, 40.0, 40.0)
+    kept = ox.forest_quasar_pairs(cat, q, bins, own)
+    a = np.repeat(np.arange(cat.n_forests), q.n)
+    k = np.tile(np.arange(q.n), cat.n_forests)
+    m = k != own[a]
+    everything = (a[m], k[m])
+    assert len(kept[0]) < 0.9 * len(everything[0])
+    r1 = ox.xcf_sums(cat, q, bins, kept, eps_edge=1e-3)
+    r2 = ox.xcf_sums(cat, q, bins, everything, eps_edge=1e-3)
+    for key in ("wsum", "num", "count", "edge_w"):
+        np.testing.assert_array_equal(r1[key], r2[key])
+    assert r1["count"].sum() > 1000
