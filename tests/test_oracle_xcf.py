@@ -5,7 +5,6 @@ on a bin-constant field, and the projector identities of Eq. (2.7)."""
 import math
 
 import numpy as np
-import pytest
 
 from conftest import line_catalog, random_small
 from oracle import xcf as ox, xi1d as o1, xi as oxi, project as oproj
