@@ -1,14 +1,16 @@
-"""Gradient of L = sum_A c_A xi_A with respect to delta and w.
+"""Gradient of L = sum_A c_A xi_A + sum_A e_A W_A with respect to delta and w.
 
 Not in the paper; it is the chain rule applied to Eq. (2.4).  With
 N_A = sum_A (w d)_i (w d)_j, W_A = sum_A w_i w_j, xi_A = N_A / W_A,
-gamma_A = c_A / W_A and rho_A = gamma_A xi_A (both 0 where W_A = 0):
+gamma_A = c_A / W_A and rho_A = gamma_A xi_A - e_A (gamma and gamma xi are 0
+where W_A = 0):
 
     dL/d delta_i = w_i      sum_{j paired with i in grid} gamma_A (w d)_j
     dL/d w_i     = delta_i  sum_j gamma_A (w d)_j  -  sum_j rho_A w_j
 
 where A is the bin of the pair (i, j) and j runs over pixels of the other
-forest of every forest pair containing i.
+forest of every forest pair containing i.  The e_A term is dW_A/dw_i =
+sum_{j in A} w_j, the weight sum's own dependence on w.
 """
 from __future__ import annotations
 
@@ -20,8 +22,9 @@ from . import pairs as _pairs
 
 
 def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None, absolute: bool = False,
-            eps_edge: float = 0.0, fwd=None):
-    """(dL/d delta, dL/d w, forward sums) for L = sum_A grad_xi[A] xi_A.
+            eps_edge: float = 0.0, fwd=None, grad_wsum=None):
+    """(dL/d delta, dL/d w, forward sums) for
+    L = sum_A grad_xi[A] xi_A + sum_A grad_wsum[A] W_A (grad_wsum default 0).
 
     With ``absolute`` the forward dict also holds the same sums taken over the
     absolute values of the terms (the scale of rounding effects).  With
@@ -40,6 +43,8 @@ def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None, absolute: bool = Fal
     g = np.asarray(grad_xi, dtype=np.float64)
     gamma = np.divide(g, W, out=np.zeros_like(W), where=W != 0)
     rho = gamma * fwd["xi"]
+    if grad_wsum is not None:
+        rho = rho - np.asarray(grad_wsum, dtype=np.float64)
     gd = np.zeros(cat.n_pix)
     gw = np.zeros(cat.n_pix)
     gda = np.zeros(cat.n_pix)
@@ -103,11 +108,15 @@ def xi_grad(cat, bins, grad_xi, pair_list=None, delta=None, absolute: bool = Fal
     return gd, gw, fwd
 
 
-def loss(cat, bins, grad_xi, pair_list=None, delta=None, weight=None) -> float:
-    """L = sum_A c_A xi_A, with optional replacement delta / weight arrays."""
+def loss(cat, bins, grad_xi, pair_list=None, delta=None, weight=None, grad_wsum=None) -> float:
+    """L = sum_A c_A xi_A (+ sum_A e_A W_A with e = grad_wsum), with optional
+    replacement delta / weight arrays."""
     if weight is not None:
         import copy
         cat = copy.copy(cat)
         cat.weight = np.asarray(weight)
     out = xi_sums(cat, bins, pair_list, delta=delta)
-    return float(np.dot(np.asarray(grad_xi, dtype=np.float64), out["xi"]))
+    L = float(np.dot(np.asarray(grad_xi, dtype=np.float64), out["xi"]))
+    if grad_wsum is not None:
+        L += float(np.dot(np.asarray(grad_wsum, dtype=np.float64), out["wsum"]))
+    return L

@@ -113,24 +113,12 @@ def xi_sums(cat, bins, pair_list=None, delta=None, eps_edge: float = 0.0,
     return out
 
 
-def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0):
-    """Per-bin weighted means of the separations and of the pair distance, and
-    pixel-pair counts, over the pixel pairs of Eq. (2.4):
-
-        rpar_mean_A  = sum_A w_i w_j r_par / W_A,   rperp_mean_A = sum_A w_i w_j r_perp / W_A,
-        dist_mean_A  = sum_A w_i w_j (d_i + d_j) / 2 / W_A,   count_A = number of pairs in A,
-
-    0 where W_A = 0.  These are the per-bin columns a PICCA/Vega fit reads next
-    to xi (the paper exports its results for Vega, Appendix A); the redshift of
-    a bin follows from dist_mean through the caller's d(z).  With eps_edge > 0
-    also ``edge_c``, the number of pairs within eps of an edge per candidate
-    bin (as ``edge_w`` counts their weight)."""
-    if pair_list is None:
-        pair_list = _pairs.forest_pairs(cat, bins)
+def _means_chunk(cat, bins, a_arr, b_arr, extra):
+    eps_edge = extra.get("eps_edge", 0.0)
     nb = bins.nbins
     W, WP, WT, WD, cnt, ew, ec = (np.zeros(nb) for _ in range(7))
     nvec = unit_vectors(cat.ra, cat.dec)
-    for a, b in zip(*pair_list):
+    for a, b in zip(a_arr, b_arr):
         sa, sb = cat.forest(a), cat.forest(b)
         if sa.stop == sa.start or sb.stop == sb.start:
             continue
@@ -160,6 +148,26 @@ def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0):
                     idx = (pp[m] * bins.n_perp + tt[m]).astype(np.int64)
                     ew += np.bincount(idx, weights=aw[m], minlength=nb)
                     ec += np.bincount(idx, minlength=nb)
+    return {"W": W, "WP": WP, "WT": WT, "WD": WD, "count": cnt, "edge_w": ew, "edge_c": ec}
+
+
+def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0, processes: int = 1):
+    """Per-bin weighted means of the separations and of the pair distance, and
+    pixel-pair counts, over the pixel pairs of Eq. (2.4):
+
+        rpar_mean_A  = sum_A w_i w_j r_par / W_A,   rperp_mean_A = sum_A w_i w_j r_perp / W_A,
+        dist_mean_A  = sum_A w_i w_j (d_i + d_j) / 2 / W_A,   count_A = number of pairs in A,
+
+    0 where W_A = 0.  These are the per-bin columns a PICCA/Vega fit reads next
+    to xi (the paper exports its results for Vega, Appendix A); the redshift of
+    a bin follows from dist_mean through the caller's d(z).  With eps_edge > 0
+    also ``edge_c``, the number of pairs within eps of an edge per candidate
+    bin (as ``edge_w`` counts their weight)."""
+    if pair_list is None:
+        pair_list = _pairs.forest_pairs(cat, bins)
+    a, b = pair_list
+    t = map_pairs(_means_chunk, cat, bins, a, b, {"eps_edge": float(eps_edge)}, processes=processes)
+    W = t["W"]
     div = lambda v: np.divide(v, W, out=np.zeros_like(W), where=W != 0)
-    return {"wsum": W, "rpar_mean": div(WP), "rperp_mean": div(WT), "dist_mean": div(WD), "count": cnt,
-            "edge_w": ew, "edge_c": ec}
+    return {"wsum": W, "rpar_mean": div(t["WP"]), "rperp_mean": div(t["WT"]), "dist_mean": div(t["WD"]),
+            "count": t["count"], "edge_w": t["edge_w"], "edge_c": t["edge_c"]}

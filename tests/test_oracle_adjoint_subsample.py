@@ -45,6 +45,37 @@ def test_grad_weight_central_difference(small):
         assert fd == pytest.approx(gw[i], rel=1e-5, abs=1e-9 * max(1.0, abs(gw).max()))
 
 
+def test_grad_weight_with_weight_sum_term_central_difference(small):
+    """L = sum c_A xi_A + sum e_A W_A: the W term adds sum_j e_A w_j to dL/dw_i
+    and nothing to dL/d delta_i (W does not depend on delta)."""
+    cat, bins, pr, c = small
+    e = np.random.default_rng(306).normal(size=bins.nbins) * 1e-3
+    w0 = cat.weight.astype(np.float64)
+    gd0, _, _ = adjoint.xi_grad(cat, bins, c, pr)
+    gd, gw, _ = adjoint.xi_grad(cat, bins, c, pr, grad_wsum=e)
+    np.testing.assert_array_equal(gd, gd0)
+    rng = np.random.default_rng(307)
+    for i in rng.choice(cat.n_pix, 12, replace=False):
+        h = 1e-3 * w0[i]
+        wp, wm = w0.copy(), w0.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (adjoint.loss(cat, bins, c, pr, weight=wp, grad_wsum=e)
+              - adjoint.loss(cat, bins, c, pr, weight=wm, grad_wsum=e)) / (2 * h)
+        assert fd == pytest.approx(gw[i], rel=1e-5, abs=1e-9 * max(1.0, abs(gw).max()))
+    # with c = 0 the gradient is exactly dW/dw contracted with e: sum over partners j of e_A w_j,
+    # which FD gets up to the rounding of the two losses (W is linear in each w_i)
+    z = np.zeros(bins.nbins)
+    _, gw_e, _ = adjoint.xi_grad(cat, bins, z, pr, grad_wsum=e)
+    for i in rng.choice(cat.n_pix, 6, replace=False):
+        wp, wm = w0.copy(), w0.copy()
+        wp[i] += 0.5
+        wm[i] -= 0.5
+        fd = adjoint.loss(cat, bins, z, pr, weight=wp, grad_wsum=e) - adjoint.loss(cat, bins, z, pr, weight=wm,
+                                                                                      grad_wsum=e)
+        assert fd == pytest.approx(gw_e[i], rel=1e-7, abs=1e-15)
+
+
 def test_grad_zero_for_pixels_without_pairs():
     # forest 0 far from the others: no in-grid pair, zero gradient
     from conftest import line_catalog

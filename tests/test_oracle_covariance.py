@@ -20,6 +20,28 @@ def test_base_pixels_at_nside_1():
     assert ocov.ang2pix_nest(1, np.array([-1.0]), np.array([0.1]))[0] == 8
 
 
+def test_face_orientation_of_the_nested_numbering():
+    """Within a base pixel the nested index interleaves x (even bits) and y
+    (odd bits), x counting from the pixel's southern corner toward its eastern
+    corner and y toward its western corner (the HEALPix grid of Gorski et al.
+    2005).  At nside 2 the four sub-pixels of a base pixel f are 4f (south),
+    4f+1 (east), 4f+2 (west) and 4f+3 (north).  Base pixel 4 spans longitudes
+    -pi/4 .. pi/4 on the equator, so its east and west sub-pixels have their
+    centres at longitudes +pi/8 and -pi/8; base pixel 0 has its western corner
+    at (z = 2/3, phi = 0) and its eastern corner at (z = 2/3, phi = pi/2).
+    Swapping x and y exchanges 4f+1 and 4f+2, which these points tell apart."""
+    eq = ocov.ang2pix_nest(2, np.zeros(4), np.array([math.pi / 8, -math.pi / 8, 0.01, -0.01]))
+    np.testing.assert_array_equal(eq, [17, 18, 17, 18])
+    # equator, just above and below phi = 0 on the south / north halves
+    assert ocov.ang2pix_nest(2, np.array([-0.3]), np.array([0.0]))[0] == 16
+    assert ocov.ang2pix_nest(2, np.array([0.3]), np.array([0.0]))[0] == 19
+    # polar base pixel 0 near its east and west corners (z just below 2/3)
+    pol = ocov.ang2pix_nest(2, np.full(2, 0.66), np.array([math.pi / 2 - 0.02, 0.02]))
+    np.testing.assert_array_equal(pol, [1, 2])
+    # and near its north corner, the pole
+    assert ocov.ang2pix_nest(2, np.array([0.999]), np.array([math.pi / 4]))[0] == 3
+
+
 @pytest.mark.parametrize("nside", [1, 2, 4, 8, 16, 32, 64])
 def test_nested_hierarchy(nside):
     """In the nested scheme pixel p at nside splits into 4p .. 4p+3 at 2 nside."""
