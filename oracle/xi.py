@@ -115,8 +115,9 @@ def xi_sums(cat, bins, pair_list=None, delta=None, eps_edge: float = 0.0,
 
 def _means_chunk(cat, bins, a_arr, b_arr, extra):
     eps_edge = extra.get("eps_edge", 0.0)
+    zpix = extra.get("z")
     nb = bins.nbins
-    W, WP, WT, WD, cnt, ew, ec = (np.zeros(nb) for _ in range(7))
+    W, WP, WT, WD, WZ, cnt, ew, ec = (np.zeros(nb) for _ in range(8))
     nvec = unit_vectors(cat.ra, cat.dec)
     for a, b in zip(a_arr, b_arr):
         sa, sb = cat.forest(a), cat.forest(b)
@@ -132,6 +133,9 @@ def _means_chunk(cat, bins, a_arr, b_arr, extra):
         WP += np.bincount(Ai, weights=(tw * r_par)[ok], minlength=nb)
         WT += np.bincount(Ai, weights=(tw * r_perp)[ok], minlength=nb)
         WD += np.bincount(Ai, weights=(tw * dm)[ok], minlength=nb)
+        if zpix is not None:
+            zm = 0.5 * (np.asarray(zpix[sa], dtype=np.float64)[:, None] + np.asarray(zpix[sb], dtype=np.float64)[None, :])
+            WZ += np.bincount(Ai, weights=(tw * zm)[ok], minlength=nb)
         cnt += np.bincount(Ai, minlength=nb)
         if eps_edge > 0.0:
             p_lo = np.floor(np.maximum(x - eps_edge, 0.0))
@@ -148,10 +152,10 @@ def _means_chunk(cat, bins, a_arr, b_arr, extra):
                     idx = (pp[m] * bins.n_perp + tt[m]).astype(np.int64)
                     ew += np.bincount(idx, weights=aw[m], minlength=nb)
                     ec += np.bincount(idx, minlength=nb)
-    return {"W": W, "WP": WP, "WT": WT, "WD": WD, "count": cnt, "edge_w": ew, "edge_c": ec}
+    return {"W": W, "WP": WP, "WT": WT, "WD": WD, "WZ": WZ, "count": cnt, "edge_w": ew, "edge_c": ec}
 
 
-def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0, processes: int = 1):
+def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0, processes: int = 1, z=None):
     """Per-bin weighted means of the separations and of the pair distance, and
     pixel-pair counts, over the pixel pairs of Eq. (2.4):
 
@@ -159,15 +163,23 @@ def bin_means(cat, bins, pair_list=None, eps_edge: float = 0.0, processes: int =
         dist_mean_A  = sum_A w_i w_j (d_i + d_j) / 2 / W_A,   count_A = number of pairs in A,
 
     0 where W_A = 0.  These are the per-bin columns a PICCA/Vega fit reads next
-    to xi (the paper exports its results for Vega, Appendix A); the redshift of
-    a bin follows from dist_mean through the caller's d(z).  With eps_edge > 0
+    to xi (the paper exports its results for Vega, Appendix A).  With ``z``, a
+    per-pixel redshift array of the catalogue's pixels, also the bin's mean
+    redshift  z_mean_A = sum_A w_i w_j (z_i + z_j) / 2 / W_A  (the redshift of a
+    pixel pair is the mean of its two pixels' redshifts).  With eps_edge > 0
     also ``edge_c``, the number of pairs within eps of an edge per candidate
     bin (as ``edge_w`` counts their weight)."""
     if pair_list is None:
         pair_list = _pairs.forest_pairs(cat, bins)
     a, b = pair_list
-    t = map_pairs(_means_chunk, cat, bins, a, b, {"eps_edge": float(eps_edge)}, processes=processes)
+    extra = {"eps_edge": float(eps_edge)}
+    if z is not None:
+        extra["z"] = np.asarray(z, dtype=np.float64)
+    t = map_pairs(_means_chunk, cat, bins, a, b, extra, processes=processes)
     W = t["W"]
     div = lambda v: np.divide(v, W, out=np.zeros_like(W), where=W != 0)
-    return {"wsum": W, "rpar_mean": div(t["WP"]), "rperp_mean": div(t["WT"]), "dist_mean": div(t["WD"]),
-            "count": t["count"], "edge_w": t["edge_w"], "edge_c": t["edge_c"]}
+    out = {"wsum": W, "rpar_mean": div(t["WP"]), "rperp_mean": div(t["WT"]), "dist_mean": div(t["WD"]),
+           "count": t["count"], "edge_w": t["edge_w"], "edge_c": t["edge_c"]}
+    if z is not None:
+        out["z_mean"] = div(t["WZ"])
+    return out

@@ -91,3 +91,30 @@ def test_bin_means_edge_counts_bound_rebinning():
         changed |= bool(np.any(alt["count"] != ref["count"]))
     assert ref["count"].sum() > 50
     assert changed or ref["edge_c"].sum() == 0
+
+
+def test_bin_mean_redshift_hand_built_and_linear_identity():
+    """Mean redshift of a bin: (a) the hand-built pairs of the first test with
+    pixel redshifts 2.0, 2.1 (a) and 2.2, 2.3 (b): bin (0, 0) holds (i0, j0) and
+    (i1, j0) with weights 3 and 6, so z = (3 (2.0 + 2.2) / 2 + 6 (2.1 + 2.2) / 2) / 9;
+    (b) a pixel redshift linear in distance, z = alpha + beta d, gives exactly
+    alpha + beta dist_mean in every bin; (c) a constant z gives that constant."""
+    th = 2 * math.asin(1e-4)
+    cat = line_catalog([(0.0, math.pi / 2, [1000.0, 1003.0], [8.0, 8.1], [0.1, 0.2], [1.0, 2.0]),
+                        (0.0, math.pi / 2 - th, [1001.0, 1010.0], [8.0, 8.1], [0.3, 0.4], [3.0, 5.0])])
+    bins = synth.Bins(4, 4, 16.0, 16.0)
+    z = np.array([2.0, 2.1, 2.2, 2.3])
+    out = oxi.bin_means(cat, bins, (np.array([0]), np.array([1])), z=z)
+    assert out["z_mean"][0] == pytest.approx((3 * 2.1 + 6 * 2.15) / 9, rel=1e-14)
+    assert out["z_mean"][4] == pytest.approx((2.1 + 2.3) / 2, rel=1e-14)
+    big = synth.make(0)
+    bb = synth.bins_for(0)
+    from oracle import pairs as opairs
+    pl = opairs.forest_pairs(big, bb)
+    sub = (pl[0][::60], pl[1][::60])
+    lin = oxi.bin_means(big, bb, sub, z=1.7 + 2.5e-4 * big.dist)
+    on = lin["wsum"] > 0
+    np.testing.assert_allclose(lin["z_mean"][on], 1.7 + 2.5e-4 * lin["dist_mean"][on], rtol=1e-13)
+    const = oxi.bin_means(big, bb, sub, z=np.full(big.n_pix, 2.4))
+    np.testing.assert_allclose(const["z_mean"][on], 2.4, rtol=1e-14)
+    assert np.all(const["z_mean"][~on] == 0)
