@@ -1,11 +1,16 @@
 #!/usr/bin/env python
 """Throughput of the Lyman-alpha pixel-pair hot path on GB300.
 
-One step = one pass of the whole path over the SDSS-DR16-like workload
-(60,000 forests over 2,500 deg^2, 50 x 50 bins of 4 Mpc/h): continuum
-projection, pair-list build, xi/W (mixed precision), distortion matrix on a
-seeded 5% forest-pair subsample, and the xi adjoint.  `value` is in-grid
-pixel pairs of the xi/W sum per second of step time.  Prints one JSON line.
+Default workload: the DESI-Y5-like catalogue, 600,000 forests over
+10,000 deg^2 on a linear 0.8 A grid (100-600 pixels per forest, a continuum
+tilt projected out), 50 x 50 bins of 4 Mpc/h.  One step = continuum
+projection + pair-list build + xi/W (mixed precision) over the whole
+catalogue.  `value` is in-grid pixel pairs of the xi/W sum per second of step
+time.  Beside it: the plain-FP64 path on a seeded 0.5% sample of the forest
+pairs, the xi kernel's roofline, the end-to-end rate through the C ABI from
+host buffers, the CPU FP64 oracle on a slice of the same catalogue, a
+graph-replay comparison, and (extra key `sdss_60k_step`) the SDSS-DR16-like
+step with the distortion matrix and the adjoint.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -216,16 +221,90 @@ def time_oracle(cat, bins, target_pixel_pairs: float, processes: int = 0):
                       f"{dt:.1f} s on {procs} processes"}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_slice(cat, bins, target_candidates: float):
+    """The forest pairs of the catalogue that have a forest inside a small cap
+    around the catalogue centre (the pole), every partner included, each pair
+    once.  The cap is grown until the slice holds about `target_candidates`
+    candidate pixel pairs.  Returns (sub-catalogue, local pairs, candidates,
+    cap radius in degrees, forests in the cap)."""
+    import oracle
+    from paper_2507_00129_gb300 import synth
+    n = oracle.geometry.unit_vectors(cat.ra, cat.dec)
+    ang = np.degrees(np.arccos(np.clip(n[:, 2], -1.0, 1.0)))
+    order = np.argsort(ang)
+    dmin = float(cat.dist.min())
+    th_max = np.degrees(2.0 * np.arcsin(min(1.0, bins.r_perp_max / (2.0 * dmin))))
+    k = 8
+    while True:
+        rad = float(ang[order[k - 1]])
+        near = np.nonzero(ang <= rad + th_max + 1e-9)[0]
+        sub = synth.subset(cat, near)
+        a, b = oracle.pairs.forest_pairs(sub, bins)
+        inside = ang[near] <= rad
+        keep = inside[a] | inside[b]
+        a, b = a[keep], b[keep]
+        L = sub.lengths()
+        cand = float(np.sum(L[a].astype(float) * L[b]))
+        if cand >= target_candidates or k >= len(order):
+            return sub, (a, b), cand, rad, int(inside.sum())
+        k = int(k * 1.3) + 1
+
+
+def time_oracle_slice(cat, bins, target_candidates: float, total_pixel_pairs: float, processes: int = 0):
+    """The CPU FP64 oracle on a slice of the catalogue (oracle_slice), on all
+    host cores: in-grid pixel pairs per second, and the full catalogue's time
+    extrapolated from that rate."""
+    import oracle
+    sub, pr, cand, rad, n_in = oracle_slice(cat, bins, target_candidates)
+    procs = processes if processes > 0 else (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    out = oracle.xi.xi_sums(sub, bins, pr, processes=procs)
+    dt = time.perf_counter() - t0
+    pix = float(out["count"].sum())
+    rate = pix / dt
+    return {"value": rate, "unit": "pixel pairs/s", "cores": procs, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"xi/W of the {len(pr[0])} forest pairs with a forest within {rad:.2f} deg of the "
+                      f"catalogue centre ({n_in} forests), all partners: {pix:.3g} in-grid of {cand:.3g} "
+                      f"candidate pixel pairs, {dt:.1f} s on {procs} processes",
+            "extrapolated_full_catalogue_s": total_pixel_pairs / rate,
+            "extrapolated": "full-catalogue time = its in-grid pixel pairs / the slice's rate"}
+
+
 def run_reference(args, rank, world):
+    """The reference arm of this tier: the CPU FP64 oracle on the default
+    workload's catalogue, each step a bounded slice of it (oracle_slice)."""
     if rank != 0:
         return
     from paper_2507_00129_gb300 import synth
-    cat = synth.make(1)
-    bins = synth.bins_for(1)
+    spec = synth.spec_for(2, seed=2)
+    if args.forests:
+        spec.area_deg2 = spec.area_deg2 * args.forests / spec.n_forests
+        spec.n_forests = args.forests
+    cat = synth.generate(spec, name="desi_like")
+    bins = synth.bins_for(2)
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
-        r = time_oracle(cat, bins, 3e9)
+        r = time_oracle_slice(cat, bins, 2e9, float("nan"))
         if k >= args.warmup:
             vals.append(r["value"])
             info = r
@@ -233,9 +312,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pixel pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, impl="CPU FP64 oracle (bounded sample per step)"),
+            "config": dict(WORKLOAD_DESI, impl="CPU FP64 oracle (bounded slice per step)"),
             "cpu_baseline": {"value": v, "unit": "pixel pairs/s", "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"]},
+                             "cpu_model": info["cpu_model"], "sample": info["sample"]},
             "e2e": {"value": v, "unit": "pixel pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -243,7 +322,11 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def run_ours(args, rank, world, local):
+def sdss_step(args, rank, world, local, steps: int, warmup: int, full: bool = True):
+    """The SDSS-DR16-like step (60,000 forests, 50 x 50 bins to 200 Mpc/h):
+    project + pair list + xi/W (mixed) + D (5%) + adjoint.  Returns the JSON
+    line's fields; with full=False (the default workload's extra key) the
+    end-to-end, plain-FP64, CPU and graph measurements are left out."""
     import torch
     from paper_2507_00129_gb300 import synth, build
     build.build()
@@ -272,6 +355,7 @@ def run_ours(args, rank, world, local):
     api.lya_project(h, dc, out=delta_p)
     st = api.lya_pair_stats(h, dcp, bins, 1.0)
     dm = api.lya_pair_stats(h, dcp, bins, DM_P, DM_SEED)
+    dmw = api.lya_dmat_work(h, dcp, bins, DM_P, DM_SEED)
     tune = api.lya_autotune(h, dcp, bins)
 
     def step():
@@ -282,7 +366,7 @@ def run_ours(args, rank, world, local):
         gd, gw = api.lya_xi_backward(h, dcp, bins, g, xi, wsum)
         return D, gd, gw
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     barrier(world)
@@ -294,7 +378,7 @@ def run_ours(args, rank, world, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
             for k in stage:
                 stage[k].append(api.lya_stage_ms(h, k))
@@ -302,15 +386,58 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         barrier(world)
     launches = api.lya_kernel_launches() - launches0
-    ms_local = e0.elapsed_time(e1) / args.steps
+    ms_local = e0.elapsed_time(e1) / steps
     ms, pix_total, value = aggregate(ms_local, float(st["pixel_pairs"]), world)
     med = {k: float(np.median(v)) for k, v in stage.items()}
+    pk, how = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
+    ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
+    ach_dm = dmw["flops"] / (med["dmat"] / 1e3) / 1e12
+    dm_line = {"pair_pairs_per_s": dm["pixel_pairs_sq"] / (med["dmat"] / 1e3),
+               "pair_pairs": dm["pixel_pairs_sq"], "forest_pairs": dm["forest_pairs"],
+               "pixel_pairs": dm["pixel_pairs"],
+               "closed_form_flops": dmw["flops"], "sum_vec_support_sq": dmw["sum_vec_support_sq"],
+               "sum_pair_support_sq": dmw["sum_pair_support_sq"],
+               "roofline_dm": {"bound": "alu", "kernel": "dm_kernel", "achieved": ach_dm, "peak": peak_fp32,
+                               "unit": "TFLOP/s", "frac": ach_dm / peak_fp32,
+                               "flops_note": "20 per in-grid pixel pair + 4 sum |S_v|^2 + 8 sum |S_pair|^2 "
+                                             "(lya_dmat_work), over the D stage's device time"}}
+    # the same D stage with the rank-1 tiles on the tensor cores (TF32x3) instead of FP32 FMA
+    tiles = {"fp32_fma_ms": med["dmat"]}
+    try:
+        api.lya_set_dmat_tiles(h, "tf32x3")
+        api.lya_dmat(h, dcp, bins, DM_P, DM_SEED)
+        tt = []
+        for _ in range(2):
+            api.lya_dmat(h, dcp, bins, DM_P, DM_SEED)
+            tt.append(api.lya_stage_ms(h, "dmat"))
+        tiles["tf32x3_tensor_ms"] = float(np.median(tt))
+    finally:
+        api.lya_set_dmat_tiles(h, "fp32")
+    dm_line["rank1_tiles"] = tiles
+    if not full:
+        flips = api.lya_flip_tally(h, dcp, bins, 0.01, 99)
+        flips["fraction_of_weight"] = flips["flipped_weight"] / max(flips["weight"], 1e-300)
+        h.close()
+        return {"workload": "sdss_dr16_like_60k", "step": "project + pair list + xi/W mixed + D (5%) + adjoint",
+                "value": value, "unit": "pixel pairs/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                "stages_ms": med, "dominant_stage": max(med, key=med.get),
+                "xi_kernel": {"pixel_pairs_per_s": st["pixel_pairs"] / (med["xi"] / 1e3),
+                              "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"],
+                              "roofline": {"bound": "alu", "achieved": ach, "peak": peak_fp32, "unit": "TFLOP/s",
+                                           "frac": ach / peak_fp32}},
+                "dm": dm_line,
+                "adjoint": {"ms": med["adjoint"],
+                            "pixel_pair_visits_per_s": 2 * st["pixel_pairs"] / (med["adjoint"] / 1e3)},
+                "edge_flips": flips, "gpu_launches": int(launches), "clocks": clk.summary()}
 
     # end to end through the public API from pinned host memory
     host = {k: getattr(dc, k).cpu().pin_memory() for k in
             ("offsets", "ra", "dec", "dist", "loglam", "delta", "weight")}
     h2d = sum(t.numel() * t.element_size() for t in host.values())
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(steps, 3))
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
@@ -341,11 +468,6 @@ def run_ours(args, rank, world, local):
         fp64 = {"pixel_pairs_per_s": st["pixel_pairs"] / (fms / 1e3), "kernel_ms": fms,
                 "call_ms": (time.perf_counter() - f0) * 1e3}
 
-    pk, how = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s at the maximum SM clock
-    ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
     if fp64 is not None:
         # the plain-FP64 path against an FP64 peak from the DFMA rate measured on this part
         # (1.7 DFMA per SM per clock in a microbenchmark), same 8 algorithmic flops per pair
@@ -377,8 +499,8 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(cat, bins, 6e9)
     line = {
-        "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, **({"forests": args.forests} if args.forests else {}),
                        l2="inputs larger than L2 (catalogue 450 MB; packed pixels 180 MB)",
@@ -394,9 +516,7 @@ def run_ours(args, rank, world, local):
         "stages_ms": med, "dominant_stage": dominant,
         "xi_kernel": {"pixel_pairs_per_s": st["pixel_pairs"] / (med["xi"] / 1e3),
                       "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"]},
-        "dm": {"pair_pairs_per_s": dm["pixel_pairs_sq"] / (med["dmat"] / 1e3),
-               "pair_pairs": dm["pixel_pairs_sq"], "forest_pairs": dm["forest_pairs"],
-               "pixel_pairs": dm["pixel_pairs"]},
+        "dm": dm_line,
         "fp64_path": fp64,
         "edge_flips": flips,
         "covariance": covariance,
@@ -408,9 +528,14 @@ def run_ours(args, rank, world, local):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
+    h.close()
+    return line
+
+
+def run_sdss(args, rank, world, local):
+    line = sdss_step(args, rank, world, local, args.steps, args.warmup, full=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
 
 
 def graph_replay(api, synth, dev, iters: int = 20):
@@ -467,10 +592,9 @@ def graph_replay(api, synth, dev, iters: int = 20):
             "iters": iters}
 
 
-def run_desi(args, rank, world, local):
-    """The DESI-Y5-like catalogue (600,000 forests): project + pair list +
-    xi/W (mixed) per step, and the plain-FP64 path beside the mixed one on a
-    seeded 0.5% sample of the forest pairs."""
+def run_ours(args, rank, world, local):
+    """The default line: the DESI-Y5-like catalogue (600,000 forests), one step
+    = project + pair list + xi/W (mixed) over the whole catalogue."""
     import torch
     from paper_2507_00129_gb300 import synth, build
     build.build()
@@ -488,7 +612,6 @@ def run_desi(args, rank, world, local):
     bins = synth.bins_for(2)
     nb = bins.nbins
     dc = api.DeviceCatalog.from_host(cat, device=dev)
-    del cat
     h = api.Handle()
     dp = torch.empty_like(dc.delta)
     dcp = dc.with_(delta=dp)
@@ -503,6 +626,7 @@ def run_desi(args, rank, world, local):
     del tcat
     api.lya_project(h, dc, out=dp)
     st = api.lya_pair_stats(h, dcp, bins, 1.0)
+    max_len = int(cat.lengths().max())
 
     def step():
         api.lya_project(h, dc, out=dp)
@@ -533,54 +657,147 @@ def run_desi(args, rank, world, local):
     ms, pix_total, value = aggregate(ms_local, float(st["pixel_pairs"]), world)
     med = {k: float(np.median(v)) for k, v in stage.items()}
 
+    # end to end through the C ABI: pinned host catalogue -> device, the step,
+    # xi and W back to the host
+    host = {k: getattr(dc, k).cpu().pin_memory() for k in
+            ("offsets", "ra", "dec", "dist", "loglam", "delta", "weight")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    e2e_steps = max(1, min(args.steps, 2))
+    devt = {k: torch.empty_like(getattr(dc, k)) for k in host}
+    dce = api.DeviceCatalog(**devt)
+    dpe = torch.empty_like(dce.delta)
+    dcep = dce.with_(delta=dpe)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, v in host.items():
+            devt[k].copy_(v, non_blocking=True)
+        api.lya_project(h, dce, out=dpe)
+        api.lya_pairs_build(h, dcep, bins)
+        n_, w_, x_ = api.lya_xi(h, dcep, bins, "mixed")
+        outs = [x_.cpu(), w_.cpu()]
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    d2h = sum(t.numel() * t.element_size() for t in outs)
+    del devt, dce, dpe, dcep
+
+    # graph replay of project + xi/W (the pair list is cached between replays)
+    graph = None if args.no_graph else graph_replay_large(api, h, dc, dp, dcp, bins, num, wsum, xi, dev)
+
     # plain FP64 beside mixed on a seeded 0.5% sample of the forest pairs
-    n = api.lya_pairs_build(h, dcp, bins)
-    pa, pb = api.lya_pairs_get(h, n)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(7)
-    sel = torch.rand(n, generator=gen, device=dev) < 0.005
-    sa, sb = pa[sel].contiguous(), pb[sel].contiguous()
-    del pa, pb, sel
-    sub = {}
-    for prec in ("mixed", "fp64"):
-        api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
-        torch.cuda.synchronize()
-        api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
-        sub[prec] = api.lya_stage_ms(h, "xi")
-    # in-grid pixel pairs of the sample (counted with the mixed binning)
-    _, wcount, _ = api.lya_xi_pairs(h, dcp.with_(weight=torch.ones_like(dc.weight)), bins, sa, sb, "mixed")
-    sample_pix = float(wcount.sum())
+    fp64 = None
+    if not args.no_fp64:
+        n = api.lya_pairs_build(h, dcp, bins)
+        pa, pb = api.lya_pairs_get(h, n)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        sel = torch.rand(n, generator=gen, device=dev) < 0.005
+        sa, sb = pa[sel].contiguous(), pb[sel].contiguous()
+        del pa, pb, sel
+        sub = {}
+        for prec in ("mixed", "fp64"):
+            api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
+            torch.cuda.synchronize()
+            api.lya_xi_pairs(h, dcp, bins, sa, sb, prec)
+            sub[prec] = api.lya_stage_ms(h, "xi")
+        # in-grid pixel pairs of the sample (counted with the mixed binning)
+        _, wcount, _ = api.lya_xi_pairs(h, dcp.with_(weight=torch.ones_like(dc.weight)), bins, sa, sb, "mixed")
+        sample_pix = float(wcount.sum())
+        fp64 = {"sample": "seeded 0.5% of the forest pairs (torch generator seed 7)", "forest_pairs": int(sa.numel()),
+                "pixel_pairs": sample_pix, "mixed_ms": sub["mixed"], "fp64_ms": sub["fp64"],
+                "mixed_pixel_pairs_per_s": sample_pix / (sub["mixed"] / 1e3),
+                "fp64_pixel_pairs_per_s": sample_pix / (sub["fp64"] / 1e3)}
+        del sa, sb
 
     pk, how = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_fp32 = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     ach = FLOPS_PER_PAIR * st["pixel_pairs"] / (med["xi"] / 1e3) / 1e12
+    if fp64 is not None:
+        peak_fp64 = n_sm * FP64_DFMA_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+        a64 = FLOPS_PER_PAIR * fp64["fp64_pixel_pairs_per_s"] / 1e12
+        fp64["roofline"] = {"bound": "fp64", "achieved": a64, "peak": peak_fp64, "unit": "TFLOP/s",
+                            "frac": a64 / peak_fp64,
+                            "peak_note": f"{n_sm} SMs x {FP64_DFMA_PER_SM_CLK} DFMA x 2 flops x {sm_max:.0f} MHz "
+                                         "(DFMA rate measured on this GB300)"}
+    h.close()
+    del dc, dcp, dp
+    torch.cuda.empty_cache()
+
+    # the SDSS-DR16-like step with D and the adjoint (timed extra key)
+    sdss = None
+    if not args.no_sdss:
+        try:
+            sdss = sdss_step(args, rank, world, local, steps=3, warmup=2, full=False)
+        except Exception as e:  # keep the headline line
+            sdss = {"error": f"{type(e).__name__}: {e}"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle_slice(cat, bins, 3e9, float(st["pixel_pairs"]))
     line = {
         "metric": METRIC, "value": value, "unit": "pixel pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD_DESI, **({"forests": args.forests} if args.forests else {}),
-                       l2="inputs larger than L2 (catalogue 4.8 GB; packed pixels 3.2 GB)",
-                       step="project + pair list + xi/W mixed", seeds=f"catalogue seed 2+rank"),
+                       l2="inputs larger than L2 (catalogue 4.8 GB; packed pixels and prefix sums 7 GB)",
+                       step="project + pair list + xi/W mixed", seeds="catalogue seed 2+rank",
+                       fp64_path="plain-FP64 kernel on a seeded 0.5% sample of the forest pairs"),
         "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
-                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": None,
+                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": xi_traffic(spec.n_forests),
                      "peak_note": f"FP32 FMA peak {n_sm} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz "
                                   f"(sm_max of {how} peaks); {FLOPS_PER_PAIR} algorithmic flops per "
-                                  "in-grid pixel pair"},
-        "stages_ms": med,
+                                  "in-grid pixel pair; achieved over the kernel's own device time (CUDA events "
+                                  "on its stream); traffic = ncu DRAM bytes per launch scaled from a smaller "
+                                  "capture, null if the kernel changed since"},
+        "stages_ms": med, "dominant_stage": max(med, key=med.get),
         "xi_kernel": {"pixel_pairs_per_s": st["pixel_pairs"] / (med["xi"] / 1e3),
-                      "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"]},
-        "fp64_vs_mixed_on_sample": {"forest_pairs": int(sa.numel()), "pixel_pairs": sample_pix,
-                                    "mixed_ms": sub["mixed"], "fp64_ms": sub["fp64"],
-                                    "mixed_pixel_pairs_per_s": sample_pix / (sub["mixed"] / 1e3),
-                                    "fp64_pixel_pairs_per_s": sample_pix / (sub["fp64"] / 1e3)},
+                      "pixel_pairs": st["pixel_pairs"], "forest_pairs": st["forest_pairs"],
+                      "max_forest_pixels": max_len},
+        "fp64_path": fp64,
+        "graph_replay": graph,
+        "sdss_60k_step": sdss,
         "autotune_choice": tune, "generate_s": t_gen,
-        "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": None, "e2e": None,
+        "e2e": {"value": pix_total / e2e_s, "unit": "pixel pairs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": int(launches), "clocks": clk.summary(), "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
+
+
+def graph_replay_large(api, h, dc, dp, dcp, bins, num, wsum, xi, dev, iters: int = 1):
+    """Eager calls vs a replayed CUDA graph of the same calls (project + xi/W
+    on the cached pair list) on the default workload, on one side stream."""
+    import torch
+    s = torch.cuda.Stream(device=dev)
+
+    def calls():
+        api.lya_project(h, dc, out=dp, stream=s)
+        api.lya_xi(h, dcp, bins, "mixed", num, wsum, xi, stream=s)
+
+    with torch.cuda.stream(s):
+        calls()
+        api.lya_sync_status(h, s)
+        api.lya_capture_begin(h, s)
+        calls()
+        gr = api.lya_capture_end(h)
+        gr.launch(s)
+        s.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(s)
+        for _ in range(iters):
+            calls()
+        ev[1].record(s)
+        for _ in range(iters):
+            gr.launch(s)
+        ev[2].record(s)
+        s.synchronize()
+    gr.close()
+    return {"workload": "desi_y5_like_600k", "step": "project + xi/W (pair list cached)",
+            "eager_ms_per_iter": ev[0].elapsed_time(ev[1]) / iters,
+            "graph_ms_per_iter": ev[1].elapsed_time(ev[2]) / iters, "iters": iters}
 
 
 def run_mocks(args, rank, world, local):
@@ -644,6 +861,37 @@ def run_mocks(args, rank, world, local):
     ms_local = e0.elapsed_time(e1) / args.steps
     ms, pix_total, value = aggregate(ms_local, pix, world)
     med = {k: float(np.median(v)) for k, v in stage.items()}
+    # eager calls against a replayed CUDA graph of the same step (pair lists cached)
+    graph = None
+    if not args.no_graph:
+        s_ = torch.cuda.Stream(device=dev)
+        outs = {"n": torch.empty((nm, nb), dtype=torch.float64, device=dev),
+                "w": torch.empty((nm, nb), dtype=torch.float64, device=dev),
+                "x": torch.empty((nm, nb), dtype=torch.float64, device=dev)}
+
+        def calls():
+            api.lya_xi_batched(h, mocks, bins, "mixed", stream=s_, num=outs["n"], wsum=outs["w"], xi=outs["x"])
+            api.lya_dmat_batched(h, mocks, bins, p_dm, seed_dm, D=D, W=Wd, stream=s_)
+
+        with torch.cuda.stream(s_):
+            calls()
+            api.lya_sync_status(h, s_)
+            api.lya_capture_begin(h, s_)
+            calls()
+            gr = api.lya_capture_end(h)
+            gr.launch(s_)
+            s_.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(s_)
+            calls()
+            ev[1].record(s_)
+            gr.launch(s_)
+            ev[2].record(s_)
+            s_.synchronize()
+        gr.close()
+        graph = {"workload": f"mock_batch_{nm}x15k", "step": "xi/W batched + D batched (pair lists cached)",
+                 "eager_ms_per_iter": ev[0].elapsed_time(ev[1]), "graph_ms_per_iter": ev[1].elapsed_time(ev[2]),
+                 "iters": 1}
     # per-mock deviation of the batched mixed path from the plain-FP64 path (two mocks)
     dev_rows = []
     for m in range(min(2, nm)):
@@ -671,7 +919,7 @@ def run_mocks(args, rank, world, local):
         "stages_ms": med,
         "xi_kernel": {"pixel_pairs_per_s": pix / (med["xi"] / 1e3), "pixel_pairs": pix},
         "dm": {"pair_pairs_per_s": dmpp / (med["dmat"] / 1e3), "pair_pairs": dmpp, "forest_pairs": dmpairs},
-        "mixed_vs_fp64_per_mock": dev_rows, "first_call_s": first_s, "generate_s": t_gen,
+        "mixed_vs_fp64_per_mock": dev_rows, "first_call_s": first_s, "generate_s": t_gen, "graph_replay": graph,
         "autotune_choice": tune, "gpu_launches": int(launches), "clocks": clk.summary(),
         "cpu_baseline": None, "e2e": None,
     }
@@ -867,19 +1115,21 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--forests", type=int, default=0,
                     help="profiling: use this many forests (same sky density) instead of the workload's")
-    ap.add_argument("--workload", default="sdss", choices=["sdss", "desi", "mocks", "xi3", "xcf"],
-                    help="sdss: 60,000-forest SDSS-DR16-like step (default); desi: 600,000-forest DESI-Y5-like xi; "
+    ap.add_argument("--workload", default="desi", choices=["sdss", "desi", "mocks", "xi3", "xcf"],
+                    help="desi: 600,000-forest DESI-Y5-like xi step (default); sdss: 60,000-forest SDSS-DR16-like "
+                         "step with D and the adjoint; "
                          "mocks: batch of 15,000-forest mocks, xi/W + D (2%%) in one launch each; "
                          "xi3: three-point estimator on the 60,000-forest catalogue; "
                          "xcf: forest x quasar cross-correlation, its D and the 1D correlation")
     ap.add_argument("--mocks", type=int, default=128, help="mocks per rank for --workload mocks")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replay measurement")
+    ap.add_argument("--no-sdss", action="store_true", help="default workload: skip the SDSS-DR16-like extra step")
     args = ap.parse_args()
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
-    elif args.workload == "desi":
-        run_desi(args, rank, world, local)
+    elif args.workload == "sdss":
+        run_sdss(args, rank, world, local)
     elif args.workload == "mocks":
         run_mocks(args, rank, world, local)
     elif args.workload == "xi3":

@@ -185,6 +185,18 @@ int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
                     const double* grad_xi, const double* xi, const double* wsum,
                     float* grad_delta, float* grad_weight, void* stream);
 
+/* Gradient of L = sum_A grad_xi[A] xi_A + sum_A grad_wsum[A] W_A: as
+ * lya_xi_backward, with the weight sum's own dependence on w added,
+ *   dL/d w_i += sum_j grad_wsum[A] w_j   (dW_A/dw_i = sum_{j in A} w_j),
+ * i.e. gamma_A xi_A is replaced by gamma_A xi_A - grad_wsum[A] in the w
+ * gradient.  dL/d delta is unchanged (W does not depend on delta).
+ * grad_wsum: [nb] float64 device, or NULL for 0 (then this is
+ * lya_xi_backward).  The chain rule of Eq. (2.4) for both outputs of the
+ * estimator; the paper has no adjoint. */
+int lya_xi_backward_full(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* grad_xi,
+                         const double* grad_wsum, const double* xi, const double* wsum, float* grad_delta,
+                         float* grad_weight, void* stream);
+
 /* xi for n_mocks independent catalogues in one persistent launch.  mocks is a
  * host array of n_mocks catalogue descriptors (device data each); outputs are
  * [n_mocks * nb] float64, mock m at offset m*nb.  Pair lists are built per
@@ -214,6 +226,34 @@ int lya_last_launch(lya_handle* h, int64_t* n_pairs, int32_t* grid, int32_t* blo
 int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample,
                    uint64_t seed, int64_t* n_pairs, int64_t* pixel_pairs, double* pixel_pairs_sq,
                    void* stream);
+
+/* How lya_dmat and lya_dmat_batched apply the rank-1 terms of the expanded
+ * eta (Eq. 2.6 with Eq. 2.7) on the shared-memory triangle: mode 0 (default)
+ * with FP32 fused multiply-adds in 4 x 4 register tiles per thread, mode 1
+ * with the tensor cores (mma.sync m16n8k8, TF32 operands split as
+ * x = hi + lo and three products per term, about FP32 accuracy).  Bands
+ * wider than shared memory always use mode 0.  Host-only; LYA_ERR_INVALID_ARG
+ * for another mode. */
+int lya_set_dmat_tiles(lya_handle* h, int32_t mode);
+
+/* Work counts of the closed-form distortion matrix of lya_dmat (Eq. 2.6
+ * with eta of Eq. 2.7 expanded), for its roofline (synchronising): over the
+ * forest pairs kept by the subsample rule of lya_dmat, with lya_dmat's FP32
+ * binning, *n_pairs = kept forest pairs whose r_perp band reaches the grid,
+ * *pixel_pairs = their in-grid pixel pairs, *sum_vec_support_sq = the sum over
+ * every rank-1 vector (each column j of the second forest, a histogram over
+ * the first forest's pixels, and each row i of the first forest) of |S_v|^2,
+ * |S_v| being the number of distinct bins the vector touches, and
+ * *sum_pair_support_sq = the sum over pairs of |S_pair|^2, the distinct bins
+ * of all the pair's pixel pairs.  The closed form's algorithmic flops are
+ * about 20 per in-grid pixel pair (T vectors and histograms) + 4 per entry of
+ * the vectors' outer products (two rank-1 terms per vector, a multiply and an
+ * add each) + 8 |S_pair|^2 (the four T outer products).  Host outputs, any may
+ * be NULL.  LYA_ERR_CUDA if 33 * ceil(n_par n_perp / 32) words do not fit in
+ * one block's shared memory. */
+int lya_dmat_work(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample, uint64_t seed,
+                  int64_t* n_pairs, int64_t* pixel_pairs, double* sum_vec_support_sq, double* sum_pair_support_sq,
+                  void* stream);
 
 /* Per sub-sample sums for a covariance of xi (the paper takes its
  * uncertainties from sub-samples of the forests in HEALPix pixels, Sections
@@ -284,6 +324,19 @@ int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double
  * forest of shared memory. */
 int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double* wsum, double* rpar_mean,
                      double* rperp_mean, double* dist_mean, int64_t* npairs, void* stream);
+
+/* lya_xi_bin_means plus the bin's mean redshift (the redshift column of the
+ * PICCA/Vega export, Appendix A):
+ *   z_mean[A] = sum_A w_i w_j (z_i + z_j)/2 / W_A   (0 where W_A = 0),
+ * the weighted mean of the pixel pairs' mean redshifts.  z_pix: [n_pix]
+ * float64 device array of the catalogue's pixel redshifts, supplied by the
+ * caller (the library holds no cosmology or rest-frame wavelength), read as
+ * FP32 in the run sums.  z_pix and z_mean are both NULL (then this is
+ * lya_xi_bin_means) or both given.  Limit: 44 bytes per bin + 12 per pixel of
+ * the longest forest of shared memory. */
+int lya_xi_bin_means_z(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* z_pix,
+                       double* wsum, double* rpar_mean, double* rperp_mean, double* dist_mean, double* z_mean,
+                       int64_t* npairs, void* stream);
 
 /* Point tracers (quasars) for the forest x quasar cross-correlation.  Entries
  * with a non-finite or non-positive distance, non-finite position or weight,
@@ -385,9 +438,21 @@ int lya_stage_ms(lya_handle* h, int32_t stage, float* ms);
  * serialise them.
  *
  * Limits: n_forests <= 65536, n_pix <= 1048576, n_pairs <= 1048576,
+ * n_par <= 203 (the mixed pair kernel's limit), n_perp <= 4096 and
  * n_par * n_perp <= 65536; beyond them LYA_ERR_TOO_LARGE is returned before
  * any GPU work.  Arguments as for lya_xi_pairs (num/wsum may be NULL; xi needs
- * neither).  Synchronises `stream` and returns the input-check status. */
+ * neither).
+ *
+ * Status codes.  Before any GPU work: LYA_ERR_INVALID_ARG for NULL pointers,
+ * negative sizes, or r_par_max / r_perp_max not finite and > 0;
+ * LYA_ERR_TOO_LARGE for the limits above.  After the work, which this call
+ * waits for (it synchronises `stream`), it reports the device-side input
+ * checks itself, where lya_xi_pairs leaves them to lya_sync_status:
+ * LYA_ERR_UNSORTED, LYA_ERR_NONFINITE (also for a negative weight),
+ * LYA_ERR_TOO_LARGE (a forest above 2^20 pixels) and LYA_ERR_DEVICE_CHECK
+ * (inconsistent offsets, or a pair naming a forest outside [0, n_forests) or
+ * the same forest twice; such pairs are skipped).  LYA_ERR_CUDA if a CUDA call
+ * fails. */
 int lya_xi_pairs_static(const lya_catalog* cat, const lya_bins* bins, const int32_t* pair_a,
                         const int32_t* pair_b, int64_t n_pairs, double* num, double* wsum, double* xi,
                         void* stream);

@@ -71,16 +71,23 @@ SIGNATURES = {
                                  c_void_p]),
     "lya_xi_backward": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
+    "lya_xi_backward_full": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p]),
     "lya_xi_batched": (c_int, [H, CAT, c_int32, BINS, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_autotune": (c_int, [H, CAT, BINS, POINTER(c_int32), c_void_p]),
     "lya_last_launch": (c_int, [H, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32),
                                 POINTER(c_int32)]),
     "lya_pair_stats": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
                                POINTER(c_double), c_void_p]),
+    "lya_set_dmat_tiles": (c_int, [H, c_int32]),
+    "lya_dmat_work": (c_int, [H, CAT, BINS, c_double, c_uint64, POINTER(c_int64), POINTER(c_int64),
+                              POINTER(c_double), POINTER(c_double), c_void_p]),
     "lya_xi_subsamples": (c_int, [H, CAT, BINS, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xi_covariance": (c_int, [H, c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "lya_xi3": (c_int, [H, CAT, BINS3, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xi_bin_means": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lya_xi_bin_means_z": (c_int, [H, CAT, BINS, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p]),
     "lya_xcf": (c_int, [H, CAT, QSO, c_void_p, BINS, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lya_xdmat": (c_int, [H, CAT, QSO, c_void_p, BINS, c_int, c_double, c_uint64, c_void_p, c_void_p,
                           c_void_p]),

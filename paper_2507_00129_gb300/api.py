@@ -223,13 +223,28 @@ def lya_xi_backward(handle: Handle, cat: DeviceCatalog, bins, grad_xi: torch.Ten
     return gd, gw
 
 
+def lya_xi_backward_full(handle: Handle, cat: DeviceCatalog, bins, grad_xi: torch.Tensor,
+                         grad_wsum: Optional[torch.Tensor], xi: torch.Tensor, wsum: torch.Tensor, stream=None,
+                         grad_delta=None, grad_weight=None):
+    """Gradient of sum grad_xi * xi + sum grad_wsum * W (grad_wsum may be None)."""
+    gd = torch.empty_like(cat.delta) if grad_delta is None else grad_delta
+    gw = torch.empty_like(cat.weight) if grad_weight is None else grad_weight
+    g = grad_xi.to(torch.float64).contiguous()
+    e = None if grad_wsum is None else grad_wsum.to(torch.float64).contiguous()
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_xi_backward_full(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(g), _ptr(e),
+                                                     _ptr(xi.contiguous()), _ptr(wsum.contiguous()), _ptr(gd),
+                                                     _ptr(gw), _stream(stream)))
+    return gd, gw
+
+
 def lya_xi_batched(handle: Handle, mocks: Sequence[DeviceCatalog], bins, precision: str = "mixed",
-                   stream=None):
+                   stream=None, num=None, wsum=None, xi=None):
     nb = bins.n_par * bins.n_perp
     m = len(mocks)
-    num = torch.empty(m * nb, dtype=torch.float64, device="cuda")
-    wsum = torch.empty(m * nb, dtype=torch.float64, device="cuda")
-    xi = torch.empty(m * nb, dtype=torch.float64, device="cuda")
+    num = torch.empty(m * nb, dtype=torch.float64, device="cuda") if num is None else num
+    wsum = torch.empty(m * nb, dtype=torch.float64, device="cuda") if wsum is None else wsum
+    xi = torch.empty(m * nb, dtype=torch.float64, device="cuda") if xi is None else xi
     arr = (LyaCatalog * m)(*[c.c() for c in mocks])
     b = c_bins(bins)
     check(handle.h, _lib.load().lya_xi_batched(handle.h, arr, m, ctypes.byref(b), PREC[precision], _ptr(num),
@@ -260,6 +275,25 @@ def lya_pair_stats(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float 
                                                ctypes.c_uint64(seed), ctypes.byref(n), ctypes.byref(pix),
                                                ctypes.byref(sq), _stream(stream)))
     return {"forest_pairs": n.value, "pixel_pairs": pix.value, "pixel_pairs_sq": sq.value}
+
+
+def lya_set_dmat_tiles(handle: Handle, mode: str):
+    """Rank-1 tiles of the distortion-matrix kernel: "fp32" (FMA) or "tf32x3" (tensor cores)."""
+    check(handle.h, _lib.load().lya_set_dmat_tiles(handle.h, {"fp32": 0, "tf32x3": 1}[mode]))
+
+
+def lya_dmat_work(handle: Handle, cat: DeviceCatalog, bins, p_subsample: float, seed: int, stream=None) -> dict:
+    """Work counts of the closed-form distortion matrix and its algorithmic flops
+    (20 per in-grid pixel pair + 4 sum |S_v|^2 + 8 sum |S_pair|^2)."""
+    n, pix = ctypes.c_int64(0), ctypes.c_int64(0)
+    sv2, sp2 = ctypes.c_double(0), ctypes.c_double(0)
+    c, b = cat.c(), c_bins(bins)
+    check(handle.h, _lib.load().lya_dmat_work(handle.h, ctypes.byref(c), ctypes.byref(b), float(p_subsample),
+                                              int(seed), ctypes.byref(n), ctypes.byref(pix), ctypes.byref(sv2),
+                                              ctypes.byref(sp2), _stream(stream)))
+    return {"forest_pairs": n.value, "pixel_pairs": pix.value, "sum_vec_support_sq": sv2.value,
+            "sum_pair_support_sq": sp2.value,
+            "flops": 20.0 * pix.value + 4.0 * sv2.value + 8.0 * sp2.value}
 
 
 def lya_xi_subsamples(handle: Handle, cat: DeviceCatalog, bins, nside: int, stream=None):
@@ -303,17 +337,25 @@ def lya_xi3(handle: Handle, cat: DeviceCatalog, grid, stream=None):
     return num, wsum, xi
 
 
-def lya_xi_bin_means(handle: Handle, cat: DeviceCatalog, bins, stream=None):
+def lya_xi_bin_means(handle: Handle, cat: DeviceCatalog, bins, stream=None, z_pix: Optional[torch.Tensor] = None):
     """Per-bin weighted mean r_par, r_perp and pair distance, W and pixel-pair
-    counts: dict of [n_par n_perp] tensors."""
+    counts (and, with per-pixel redshifts z_pix, the mean redshift "z_mean"):
+    dict of [n_par n_perp] tensors."""
     nb = bins.n_par * bins.n_perp
-    out = {k: torch.empty(nb, dtype=torch.float64, device="cuda")
-           for k in ("wsum", "rpar_mean", "rperp_mean", "dist_mean")}
+    keys = ("wsum", "rpar_mean", "rperp_mean", "dist_mean") + (("z_mean",) if z_pix is not None else ())
+    out = {k: torch.empty(nb, dtype=torch.float64, device="cuda") for k in keys}
     out["count"] = torch.empty(nb, dtype=torch.int64, device="cuda")
     c, b = cat.c(), c_bins(bins)
-    check(handle.h, _lib.load().lya_xi_bin_means(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(out["wsum"]),
-                                                 _ptr(out["rpar_mean"]), _ptr(out["rperp_mean"]),
-                                                 _ptr(out["dist_mean"]), _ptr(out["count"]), _stream(stream)))
+    if z_pix is None:
+        check(handle.h, _lib.load().lya_xi_bin_means(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(out["wsum"]),
+                                                     _ptr(out["rpar_mean"]), _ptr(out["rperp_mean"]),
+                                                     _ptr(out["dist_mean"]), _ptr(out["count"]), _stream(stream)))
+    else:
+        z = z_pix.to(torch.float64).contiguous()
+        check(handle.h, _lib.load().lya_xi_bin_means_z(handle.h, ctypes.byref(c), ctypes.byref(b), _ptr(z),
+                                                       _ptr(out["wsum"]), _ptr(out["rpar_mean"]),
+                                                       _ptr(out["rperp_mean"]), _ptr(out["dist_mean"]),
+                                                       _ptr(out["z_mean"]), _ptr(out["count"]), _stream(stream)))
     return out
 
 
@@ -456,7 +498,8 @@ def lya_capture_end(handle: Handle) -> Graph:
 # autograd
 # ---------------------------------------------------------------------------
 class XiFunction(torch.autograd.Function):
-    """(xi, W) = estimator of Eq. (2.4) as a differentiable function of (delta, w)."""
+    """(xi, W) = estimator of Eq. (2.4) as a differentiable function of (delta, w).
+    Both outputs are differentiable: W_A = sum w_i w_j depends on w."""
 
     @staticmethod
     def forward(ctx, delta, weight, handle, cat, bins):
@@ -464,15 +507,16 @@ class XiFunction(torch.autograd.Function):
         num, wsum, xi = lya_xi(handle, c, bins, "mixed")
         ctx.handle, ctx.cat, ctx.bins = handle, c, bins
         ctx.save_for_backward(xi, wsum)
-        ctx.mark_non_differentiable(wsum)
         return xi, wsum
 
     @staticmethod
     def backward(ctx, grad_xi, grad_wsum):
         xi, wsum = ctx.saved_tensors
-        if grad_xi is None:
+        if grad_xi is None and grad_wsum is None:
             return None, None, None, None, None
-        gd, gw = lya_xi_backward(ctx.handle, ctx.cat, ctx.bins, grad_xi, xi, wsum)
+        if grad_xi is None:
+            grad_xi = torch.zeros_like(xi)
+        gd, gw = lya_xi_backward_full(ctx.handle, ctx.cat, ctx.bins, grad_xi, grad_wsum, xi, wsum)
         return gd, gw, None, None, None
 
 

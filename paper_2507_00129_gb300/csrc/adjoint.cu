@@ -2,7 +2,8 @@
 // Eq. 2.4):
 //   dL/d delta_i = w_i sum_j gamma_A (w d)_j
 //   dL/d w_i     = delta_i sum_j gamma_A (w d)_j - sum_j rho_A w_j
-// with gamma_A = g_A / W_A, rho_A = gamma_A xi_A, j over the in-grid partners of i.
+// with gamma_A = g_A / W_A, rho_A = gamma_A xi_A - e_A, j over the in-grid partners
+// of i, for L = sum_A g_A xi_A + sum_A e_A W_A (e = 0 unless given).
 //
 // Each pixel is owned by one warp (work item = 32 consecutive pixels of one
 // forest), which walks the forest's full neighbour list (both orientations of
@@ -141,7 +142,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) adjoint_kernel(AdjArgs A, cons
       const int bin = p * nperp + t;
       const double w = A.wsum[bin];
       const double g = (w != 0.0) ? A.grad_xi[bin] / w : 0.0;
-      e = make_float2(static_cast<float>(g), static_cast<float>(g * A.xi[bin]));
+      // rho = gamma xi - dL/dW (the weight sum's own dependence on w)
+      const double r = g * A.xi[bin] - (A.grad_wsum ? A.grad_wsum[bin] : 0.0);
+      e = make_float2(static_cast<float>(g), static_cast<float>(r));
     }
     table[k] = e;
   }

@@ -154,6 +154,8 @@ struct lya_handle {
   CatKey xkey;
   unsigned long long x_fp = 0, x_qfp = 0;
   unsigned long long* d_qfp = nullptr;
+  // rank-1 tiles of the distortion-matrix kernel (lya_set_dmat_tiles)
+  int dm_tensor_tiles = 0;
   // tuning and diagnostics
   int tuned_warps = 8;
   int tuned_grab = 4;
@@ -465,8 +467,8 @@ int run_xi(lya_handle* h, const lya_catalog* cats, int ncat, const lya_bins* b, 
   A.wsum = W;
   A.nb = nb;
   A.counter = h->d_counter;
-  if (prec == LYA_PREC_MIXED && b->n_par > 203)
-    return fail(h, LYA_ERR_TOO_LARGE, "the mixed path supports n_par <= 203");
+  if (prec == LYA_PREC_MIXED && b->n_par > xi_mixed_max_npar())
+    return fail(h, LYA_ERR_TOO_LARGE, "the mixed path supports n_par <= " + std::to_string(xi_mixed_max_npar()));
   if (prec == LYA_PREC_FP64 && b->n_par > 256)
     return fail(h, LYA_ERR_TOO_LARGE, "the FP64 path supports n_par <= 256");
   if (prec == LYA_PREC_MIXED) {
@@ -719,6 +721,7 @@ int run_dmat_cats(lya_handle* h, const lya_catalog* cats, int n, const lya_bins*
   A.wdm = wdm;
   A.max_len = h->max_len;
   A.n_mocks = n;
+  A.tensor_tiles = h->dm_tensor_tiles;
   A.fbase = nullptr;
   stage_begin(h, 1, s);
   CK(run_dmat(A, h->dev, &h->scratch2, &h->scratch2_cap, s), "dmat");
@@ -748,6 +751,12 @@ int lya_dmat_batched(lya_handle* h, const lya_catalog* mocks, int32_t n_mocks, c
 int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* grad_xi,
                     const double* xi, const double* wsum, float* grad_delta, float* grad_weight,
                     void* stream) {
+  return lya_xi_backward_full(h, cat, bins, grad_xi, nullptr, xi, wsum, grad_delta, grad_weight, stream);
+}
+
+int lya_xi_backward_full(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* grad_xi,
+                         const double* grad_wsum, const double* xi, const double* wsum, float* grad_delta,
+                         float* grad_weight, void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
   int st = check_bins(h, bins);
   if (st) return st;
@@ -769,6 +778,7 @@ int lya_xi_backward(lya_handle* h, const lya_catalog* cat, const lya_bins* bins,
   A.n_par = bins->n_par;
   A.n_perp = bins->n_perp;
   A.grad_xi = grad_xi;
+  A.grad_wsum = grad_wsum;
   A.xi = xi;
   A.wsum = wsum;
   A.delta = cat->delta;
@@ -906,6 +916,52 @@ int lya_pair_stats(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, 
   return LYA_OK;
 }
 
+int lya_set_dmat_tiles(lya_handle* h, int32_t mode) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (mode != 0 && mode != 1) return fail(h, LYA_ERR_INVALID_ARG, "tile mode must be 0 (FP32) or 1 (TF32x3)");
+  h->dm_tensor_tiles = mode;
+  return LYA_OK;
+}
+
+int lya_dmat_work(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample, uint64_t seed,
+                  int64_t* n_pairs, int64_t* pixel_pairs, double* sum_vec_support_sq, double* sum_pair_support_sq,
+                  void* stream) {
+  if (!h) return LYA_ERR_INVALID_ARG;
+  if (int st0 = refuse_in_capture(h, "lya_dmat_work")) return st0;
+  int st = check_bins(h, bins);
+  if (st) return st;
+  if (!(p_subsample >= 0.0) || !std::isfinite(p_subsample))
+    return fail(h, LYA_ERR_INVALID_ARG, "p_subsample must be finite and >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = prepare(h, cat, 1, s);
+  if (st) return st;
+  st = ensure_pairs(h, cat, 1, bins, s);
+  if (st) return st;
+  DmArgs A{};
+  A.pairs = static_cast<const int2*>(h->pairbuf);
+  A.cs = static_cast<const float2*>(h->csbuf);
+  A.n_pairs = h->n_pairs;
+  A.pix = static_cast<const Pix*>(h->pixbuf);
+  A.F = h->F;
+  A.n_par = bins->n_par;
+  A.n_perp = bins->n_perp;
+  A.p_subsample = p_subsample;
+  A.seed = seed;
+  A.max_len = h->max_len;
+  A.n_mocks = 1;
+  // the small device block's last 128 bytes (after d_qfp at +320) hold the counts
+  DmWork* dout = reinterpret_cast<DmWork*>(reinterpret_cast<char*>(h->d_err) + 384);
+  CK(launch_dm_work(A, h->dev, dout, s), "distortion-matrix work count");
+  DmWork host{};
+  CK(cudaMemcpyAsync(&host, dout, sizeof(DmWork), cudaMemcpyDeviceToHost, s), "read work count");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (n_pairs) *n_pairs = static_cast<int64_t>(host.pairs);
+  if (pixel_pairs) *pixel_pairs = static_cast<int64_t>(host.pix);
+  if (sum_vec_support_sq) *sum_vec_support_sq = host.sv2;
+  if (sum_pair_support_sq) *sum_pair_support_sq = host.sp2;
+  return LYA_OK;
+}
+
 int lya_flip_tally(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double p_subsample, uint64_t seed,
                    int64_t* pixel_pairs, int64_t* flipped, double* weight, double* flipped_weight, void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
@@ -1020,20 +1076,24 @@ int lya_xi3(lya_handle* h, const lya_catalog* cat, const lya_bins3* bins, double
   return LYA_OK;
 }
 
-int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double* wsum, double* rpar_mean,
-                     double* rperp_mean, double* dist_mean, int64_t* npairs, void* stream) {
+int lya_xi_bin_means_z(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, const double* z_pix,
+                       double* wsum, double* rpar_mean, double* rperp_mean, double* dist_mean, double* z_mean,
+                       int64_t* npairs, void* stream) {
   if (!h) return LYA_ERR_INVALID_ARG;
   int st = check_bins(h, bins);
   if (st) return st;
   if (!rpar_mean || !rperp_mean || !dist_mean || !npairs)
     return fail(h, LYA_ERR_INVALID_ARG, "rpar_mean, rperp_mean, dist_mean and npairs are required");
+  if ((z_pix == nullptr) != (z_mean == nullptr))
+    return fail(h, LYA_ERR_INVALID_ARG, "z_pix and z_mean go together");
   if ((st = refuse_in_capture(h, "lya_xi_bin_means"))) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = prepare(h, cat, 1, s))) return st;
   if ((st = ensure_pairs(h, cat, 1, bins, s))) return st;
   const int nb = bins->n_par * bins->n_perp;
-  if (means_smem_bytes(nb, h->max_len) > h->dev.smem_optin)
-    return fail(h, LYA_ERR_TOO_LARGE, "bin means: 36 bytes per bin + 8 per pixel of the longest forest above shared memory");
+  if (means_smem_bytes(nb, h->max_len, z_pix != nullptr) > h->dev.smem_optin)
+    return fail(h, LYA_ERR_TOO_LARGE, "bin means: 36 (44 with redshifts) bytes per bin + 8 (12) per pixel of the "
+                                      "longest forest above shared memory");
   cudaError_t e = grow(&h->scratch2, &h->scratch2_cap, means_scratch_bytes(h->F.n, h->n_pairs, nb));
   if (e != cudaSuccess) return fail(h, LYA_ERR_NO_MEMORY, "bin-means scratch");
   MeansArgs A{};
@@ -1048,10 +1108,17 @@ int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins
   A.d_perp = bins->r_perp_max / bins->n_perp;
   A.err = h->d_err;
   A.max_len = h->max_len;
+  A.zpix = z_pix;
   stage_begin(h, 0, s);
-  CK(launch_bin_means(A, h->dev, h->scratch2, wsum, rpar_mean, rperp_mean, dist_mean, npairs, s), "bin means");
+  CK(launch_bin_means(A, h->dev, h->scratch2, wsum, rpar_mean, rperp_mean, dist_mean, z_mean, npairs, s),
+     "bin means");
   stage_end(h, 0, s);
   return LYA_OK;
+}
+
+int lya_xi_bin_means(lya_handle* h, const lya_catalog* cat, const lya_bins* bins, double* wsum, double* rpar_mean,
+                     double* rperp_mean, double* dist_mean, int64_t* npairs, void* stream) {
+  return lya_xi_bin_means_z(h, cat, bins, nullptr, wsum, rpar_mean, rperp_mean, dist_mean, nullptr, npairs, stream);
 }
 
 // ---------------------------------------------------------------------------

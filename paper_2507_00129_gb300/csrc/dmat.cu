@@ -17,8 +17,9 @@
 // (r_perp is monotone in both distances), i.e. L = K n_par local bins.  The
 // kept pairs are grouped by (first band row, K); a block takes a chunk of
 // pairs of one group and keeps the upper triangle of the L x L block of D~
-// in shared memory (FP32), flushing it to the FP64 accumulator G (entries
-// A <= B) with FP64 atomics once per chunk.  The rank-1 terms are applied a
+// in shared memory (FP32): each pair's contribution is built there and added
+// to the FP64 accumulator G (entries A <= B) with FP64 atomics at the end of
+// the pair, so that the sum over pairs is FP64.  The rank-1 terms are applied a
 // batch of up to CB vectors (consecutive columns, then rows) at a time:
 //  (a1) every thread bins pixel pairs and marks the local bins the batch
 //       touches; (b) one warp compacts the marks into the batch's sorted union
@@ -132,7 +133,7 @@ constexpr int kCB = 16;   // vectors per batch
 
 // Shared-memory layout of one block (offsets in bytes)
 struct Lay {
-  int U, Wacc, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, cf, gbin, misc, end;
+  int U, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, cf, gbin, misc, end;
 };
 
 __host__ __device__ inline int scap_for(int L, int npar, int K) {
@@ -143,16 +144,25 @@ __host__ __device__ inline int scap_for(int L, int npar, int K) {
   return (c + 3) & ~3;
 }
 
+// Row stride of the batch vectors V[kCB][.]: at least the support capacity
+// rounded up to 16 (the tensor-core tiles read 16-row blocks) and 8 modulo 32,
+// so that the fragment loads of the tensor-core tiles (rows t and t + 4 of a
+// k step, 8 consecutive support entries) hit 32 different banks.
+__host__ __device__ inline int ldv_for(int scap) {
+  int v = (scap + 15) & ~15;
+  while ((v & 31) != 8) v += 8;
+  return v;
+}
+
 __host__ __device__ inline Lay layout(int L, int scap, int max_len, bool global_sink) {
   auto al = [](int v) { return (v + 15) & ~15; };
   Lay y;
   int o = 0;
   y.U = o;
   if (!global_sink) o += al(static_cast<int>((static_cast<int64_t>(L) * (L + 1) / 2) * 4));
-  y.Wacc = o; o += al(L * 4);
   y.T4 = o; o += al(L * 16);
-  y.Va = o; o += al(kCB * scap * 4);
-  y.Vb = o; o += al(kCB * scap * 4);
+  y.Va = o; o += al(kCB * ldv_for(scap) * 4);
+  y.Vb = o; o += al(kCB * ldv_for(scap) * 4);
   y.mark = o; o += al(L);
   y.inv = o; o += al(L * 2);
   y.S = o; o += al(scap * 4);
@@ -191,7 +201,7 @@ __device__ __forceinline__ int local_bin(float2 u, float dj, float cp, float sp,
 
 // Tile q of the packed upper triangle of 4 x 4 blocks of the union support:
 // acc = sum over vectors [vlo, vhi) of a a^T + b b^T on that block.
-__device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int scap, int q, int vlo, int vhi,
+__device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int ldv, int q, int vlo, int vhi,
                                         float (&acc)[4][4], int* rblk_out, int* cblk_out) {
   int rr = static_cast<int>((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
   while (rr * (rr + 1) / 2 > q) --rr;
@@ -203,10 +213,10 @@ __device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int sc
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
   for (int vv = vlo; vv < vhi; ++vv) {
-    const float4 ar = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * rblk);
-    const float4 ac = *reinterpret_cast<const float4*>(Va + vv * scap + 4 * cblk);
-    const float4 br = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * rblk);
-    const float4 bc = *reinterpret_cast<const float4*>(Vb + vv * scap + 4 * cblk);
+    const float4 ar = *reinterpret_cast<const float4*>(Va + vv * ldv + 4 * rblk);
+    const float4 ac = *reinterpret_cast<const float4*>(Va + vv * ldv + 4 * cblk);
+    const float4 br = *reinterpret_cast<const float4*>(Vb + vv * ldv + 4 * rblk);
+    const float4 bc = *reinterpret_cast<const float4*>(Vb + vv * ldv + 4 * cblk);
     const float arv[4] = {ar.x, ar.y, ar.z, ar.w}, acv[4] = {ac.x, ac.y, ac.z, ac.w};
     const float brv[4] = {br.x, br.y, br.z, br.w}, bcv[4] = {bc.x, bc.y, bc.z, bc.w};
 #pragma unroll
@@ -216,6 +226,75 @@ __device__ __forceinline__ void dm_tile(const float* Va, const float* Vb, int sc
   }
   *rblk_out = rblk;
   *cblk_out = cblk;
+}
+
+// Tensor-core form of the rank-1 tiles: C = V^T V over the union support,
+// V the batch's [32 x S] matrix (rows: the a vectors, then the b vectors),
+// with mma.sync m16n8k8 in TF32 and the 3xTF32 split (x = hi + lo, hi and lo
+// TF32; C += lo.hi + hi.lo + hi.hi), which keeps the products at about FP32
+// accuracy.  Warp tiles of 16 x 8 entries of the upper triangle (c >= r); each
+// lane subtracts its four accumulators from the triangle (entries r <= c only,
+// each unordered pair of support entries once).
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(x);
+  lo = tf32_bits(x - __uint_as_float(hi));
+}
+
+__device__ void dm_tiles_tc(const float* Va, const float* Vb, int ldv, int ns, int cbn, const int32_t* S, float* U,
+                            int L, int wid, int nwarps, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const int R = (ns + 15) >> 4, C8 = (ns + 7) >> 3;
+  const int ksteps = (cbn + 7) >> 3;   // vectors [0, cbn) in k steps of 8 (rows past cbn are zero)
+  int q = 0;
+  for (int rb = 0; rb < R; ++rb) {
+    for (int cb = 2 * rb; cb < C8; ++cb, ++q) {
+      if (q % nwarps != wid) continue;
+      const int r0 = rb * 16, c0 = cb * 8;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const float* V = half ? Vb : Va;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const float* v0 = V + (ks * 8 + t) * ldv;
+          const float* v4 = v0 + 4 * ldv;
+          uint32_t ah[4], al[4], bh[2], bl[2];
+          split_tf32(v0[r0 + g], ah[0], al[0]);
+          split_tf32(v0[r0 + g + 8], ah[1], al[1]);
+          split_tf32(v4[r0 + g], ah[2], al[2]);
+          split_tf32(v4[r0 + g + 8], ah[3], al[3]);
+          split_tf32(v0[c0 + g], bh[0], bl[0]);
+          split_tf32(v4[c0 + g], bh[1], bl[1]);
+          mma_tf32(acc, al[0], al[1], al[2], al[3], bh[0], bh[1]);
+          mma_tf32(acc, ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+          mma_tf32(acc, ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = r0 + g + ((e & 2) ? 8 : 0);
+        const int c = c0 + 2 * t + (e & 1);
+        if (r <= c && c < ns) {
+          const int lr = S[r], lc = S[c];
+          const int lo = min(lr, lc), hi = max(lr, lc);
+          U[tri_rowbase(lo, L) + hi] -= acc[e];
+        }
+      }
+    }
+  }
 }
 
 // Subtract a tile from the triangle, or from G with FP64 atomics for wide
@@ -267,6 +346,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
   const double Wa = A.F.wsum[a], Sa = A.F.ssum[a], Wb = A.F.wsum[b], Sb = A.F.ssum[b];
   const bool eta = A.eta_mean_slope != 0;
   const int npar = A.n_par, nbins = A.n_par * A.n_perp;
+  const int ldv = ldv_for(scap);
   const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(A.n_perp);
 
   float* U = reinterpret_cast<float*>(sm + y.U);
@@ -372,7 +452,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
             mark[l] = 0;
           }
         }
-        for (int k = tid; k < kCB * scap; k += blockDim.x) {
+        for (int k = tid; k < kCB * ldv; k += blockDim.x) {
           Va[k] = 0.f;
           Vb[k] = 0.f;
         }
@@ -394,7 +474,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
         const int l = local_bin(ucs[i], pxb[j].x, cp, sp, fnpar, fnperp, npar, t0);
         if (l >= 0) {
           const int2 t = tv[side == 0 ? i : j];   // the summed-over pixel's terms
-          const int k = vv_t * scap + inv[l];
+          const int k = vv_t * ldv + inv[l];
           atomicAdd(reinterpret_cast<unsigned*>(&Vai[k]), static_cast<unsigned>(t.x));
           atomicAdd(reinterpret_cast<unsigned*>(&Vbi[k]), static_cast<unsigned>(t.y));
         }
@@ -411,14 +491,14 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
         float t1 = 0.f, tx = 0.f, ty = 0.f, txy = 0.f;
         if (act) {
           const float4 c = cf[v0 + vv];
-          const float va = static_cast<float>(Vai[vv * scap + k]) * inv_scA;
-          const float vb = static_cast<float>(Vbi[vv * scap + k]) * inv_scB;
+          const float va = static_cast<float>(Vai[vv * ldv + k]) * inv_scA;
+          const float vb = static_cast<float>(Vbi[vv * ldv + k]) * inv_scB;
           t1 = c.z * va;
           tx = c.z * vb;
           ty = c.w * va;
           txy = c.w * vb;
-          Va[vv * scap + k] = va * c.x;
-          Vb[vv * scap + k] = vb * c.y;
+          Va[vv * ldv + k] = va * c.x;
+          Vb[vv * ldv + k] = vb * c.y;
         }
         if (side == 0) {
 #pragma unroll
@@ -442,13 +522,17 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
       // (d) rank-1 updates of the batch: 4 x 4 register tiles of S x S,
       // one tile per thread, each adding its 16 entries to the triangle.
       if (eta) {
-        const int nt = (ns + 3) >> 2;
-        const int ntiles = nt * (nt + 1) / 2;
-        for (int q = tid; q < ntiles; q += blockDim.x) {
-          float acc[4][4];
-          int rblk, cblk;
-          dm_tile(Va, Vb, scap, q, 0, cbn, acc, &rblk, &cblk);
-          dm_tile_store<GLOBAL>(G, U, S, gbin, ns, L, nbins, rblk, cblk, acc);
+        if (!GLOBAL && A.tensor_tiles) {
+          dm_tiles_tc(Va, Vb, ldv, ns, cbn, S, U, L, wid, blockDim.x >> 5, lane);
+        } else {
+          const int nt = (ns + 3) >> 2;
+          const int ntiles = nt * (nt + 1) / 2;
+          for (int q = tid; q < ntiles; q += blockDim.x) {
+            float acc[4][4];
+            int rblk, cblk;
+            dm_tile(Va, Vb, ldv, q, 0, cbn, acc, &rblk, &cblk);
+            dm_tile_store<GLOBAL>(G, U, S, gbin, ns, L, nbins, rblk, cblk, acc);
+          }
         }
       }
       __syncthreads();
@@ -457,13 +541,17 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
     }
   }
 
-  // T terms, diagonal and W: one warp per row r, lanes over c >= r
+  // T terms, diagonal and W: one warp per row r, lanes over c >= r.  The
+  // pair's whole contribution (its rank-1 terms, already in the triangle, plus
+  // these) goes to the FP64 accumulator here, and the triangle is cleared, so
+  // that D~ and W are summed over pairs in FP64 only.  Rows and columns with
+  // T = 0 hold nothing: every rank-1 term of a bin carries the weights of the
+  // pixel pairs in it.
   const int nwarps = blockDim.x >> 5;
   const float c11 = (eta && Wa > 0 && Wb > 0) ? static_cast<float>(1.0 / (Wa * Wb)) : 0.f;
   const float cyy = (eta && Wa > 0 && Sb > 0) ? static_cast<float>(1.0 / (Wa * Sb)) : 0.f;
   const float cxx = (eta && Sa > 0 && Wb > 0) ? static_cast<float>(1.0 / (Sa * Wb)) : 0.f;
   const float cxy = (eta && Sa > 0 && Sb > 0) ? static_cast<float>(1.0 / (Sa * Sb)) : 0.f;
-  float* Wacc = reinterpret_cast<float*>(sm + y.Wacc);
   for (int r = wid; r < L; r += nwarps) {
     const float4 tr = T4[r];
     if (tr.x == 0.f && tr.y == 0.f && tr.z == 0.f && tr.w == 0.f) continue;
@@ -478,9 +566,22 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
       const float v2 = f1 * tc2.x + fy * tc2.z + fx * tc2.y + fxy * tc2.w;
       if (c == r) v += tr.x;
       if (!GLOBAL) {
-        // (r, c), (r, c2) owned by this lane
-        if (v != 0.f) U[rb + c] += v;
-        if (v2 != 0.f) U[rb + c2] += v2;
+        // (r, c), (r, c2) owned by this lane: flush and clear
+        const int Ar = gbin[r];
+        const float t1 = U[rb + c] + v;
+        if (t1 != 0.f) {
+          const int Ac = gbin[c];
+          red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac), static_cast<double>(t1));
+          U[rb + c] = 0.f;
+        }
+        if (c2 < L) {
+          const float t2 = U[rb + c2] + v2;
+          if (t2 != 0.f) {
+            const int Ac = gbin[c2];
+            red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac), static_cast<double>(t2));
+            U[rb + c2] = 0.f;
+          }
+        }
       } else {
         const int Ar = gbin[r];
         if (v != 0.f) {
@@ -495,10 +596,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
         }
       }
     }
-    if (lane == 0) {
-      if (!GLOBAL) Wacc[r] += tr.x;
-      else red_add_f64_global(wdm + gbin[r], static_cast<double>(tr.x));
-    }
+    if (lane == 0) red_add_f64_global(wdm + gbin[r], static_cast<double>(tr.x));
   }
   __syncthreads();
   for (int k = tid; k < L; k += blockDim.x) T4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -518,7 +616,6 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
   const int n_items = GLOBAL ? *n_wide_dev : *n_chunks_dev;
   const Lay y = layout(Lalloc, scap, A.max_len, GLOBAL);
   float* U = reinterpret_cast<float*>(sm + y.U);
-  float* Wacc = reinterpret_cast<float*>(sm + y.Wacc);
   float4* T4 = reinterpret_cast<float4*>(sm + y.T4);
   unsigned char* mark = sm + y.mark;
   int32_t* gbin = reinterpret_cast<int32_t*>(sm + y.gbin);
@@ -528,7 +625,6 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     for (int k = tid; k < nt; k += blockDim.x) U[k] = 0.f;
   }
   for (int k = tid; k < Lalloc; k += blockDim.x) {
-    Wacc[k] = 0.f;
     T4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     mark[k] = 0;
   }
@@ -561,30 +657,6 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     for (int q = 0; q < cnt; ++q) {
       const int pi = GLOBAL ? wide[item] : order[first + q];
       dm_pair<GLOBAL>(A, G, wdm, pi, t0, K, L, scap, sm, y);
-    }
-    if (!GLOBAL) {
-      // flush the triangle and W of this chunk
-      const int nwarps = blockDim.x >> 5, wid = tid >> 5, lane = tid & 31;
-      for (int r = wid; r < L; r += nwarps) {
-        const int rb = tri_rowbase(r, L);
-        const int Ar = gbin[r];
-        for (int c = r + lane; c < L; c += 32) {
-          const float v = U[rb + c];
-          if (v != 0.f) {
-            const int Ac = gbin[c];
-            red_add_f64_global(G + static_cast<int64_t>(min(Ar, Ac)) * nbins + max(Ar, Ac),
-                               static_cast<double>(v));
-            U[rb + c] = 0.f;
-          }
-        }
-      }
-      for (int k = tid; k < L; k += blockDim.x) {
-        if (Wacc[k] != 0.f) {
-          red_add_f64_global(wdm + gbin[k], static_cast<double>(Wacc[k]));
-          Wacc[k] = 0.f;
-        }
-      }
-      __syncthreads();
     }
   }
 }
@@ -624,6 +696,90 @@ int grid_for(int64_t n, int threads) {
     cudaError_t e_ = (x);             \
     if (e_ != cudaSuccess) return e_; \
   } while (0)
+
+// Work counts of the closed form (one warp per kept forest pair, the D
+// kernel's FP32 binning): for every rank-1 vector (column j of b over i of a,
+// row i of a over j of b) the number |S_v| of distinct bins it touches, for
+// the pair the number |S_pair| of distinct bins of all its pixel pairs, and
+// the in-grid pixel pairs.  Bins are marked in lane-private bitmaps of the
+// pair's band (word w of lane l at w * 32 + l: no bank conflicts).
+__global__ void dm_work_kernel(DmArgs A, uint64_t thr, int all, int words_cap, DmWork* out) {
+  extern __shared__ uint32_t wbm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint32_t* mine = wbm + static_cast<size_t>(wid) * 33 * words_cap;
+  uint32_t* pbm = mine + 32 * words_cap;
+  const int npar = A.n_par;
+  const float fnpar = static_cast<float>(npar), fnperp = static_cast<float>(A.n_perp);
+  unsigned long long n_pairs = 0, n_pix = 0;
+  double sv2 = 0.0, sp2 = 0.0;
+  for (int64_t k = warp; k < A.n_pairs; k += nw) {
+    const int2 pr = A.pairs[k];
+    if (pr.x < 0 || !keep_pair(pr.x, pr.y, A.seed, thr, all)) continue;
+    const float2 cs = A.cs[k];
+    int t0, K;
+    if (!pair_band(A, pr.x, pr.y, cs.y, &t0, &K)) continue;
+    const int words = (K * npar + 31) >> 5;
+    if (words > words_cap) continue;   // (a band wider than the grid cannot occur)
+    const int na = A.F.len[pr.x], nb = A.F.len[pr.y];
+    const Pix* pa = A.pix + A.F.off[pr.x];
+    const Pix* pb = A.pix + A.F.off[pr.y];
+    const float cp = cs.x, sp = cs.y;
+    const float Dc = (A.F.dref[pr.x] - A.F.dref[pr.y]) * cp, Ds = (A.F.dref[pr.x] + A.F.dref[pr.y]) * sp;
+    for (int w = lane; w < words; w += 32) pbm[w] = 0u;
+    __syncwarp();
+    for (int side = 0; side < 2; ++side) {
+      const int nvec = side == 0 ? nb : na;
+      const int nother = side == 0 ? na : nb;
+      for (int v0 = 0; v0 < nvec; v0 += 32) {
+        const int v = v0 + lane;
+        if (v < nvec) {
+          for (int w = 0; w < words; ++w) mine[w * 32 + lane] = 0u;
+          for (int o = 0; o < nother; ++o) {
+            const int i = side == 0 ? o : v;
+            const int j = side == 0 ? v : o;
+            const float xi = pa[i].x;
+            const int l = local_bin(make_float2(fmaf(xi, cp, Dc), fmaf(xi, sp, Ds)), pb[j].x, cp, sp, fnpar,
+                                    fnperp, npar, t0);
+            if (l >= 0) {
+              mine[(l >> 5) * 32 + lane] |= 1u << (l & 31);
+              if (side == 0) ++n_pix;
+            }
+          }
+          int cnt = 0;
+          for (int w = 0; w < words; ++w) {
+            const uint32_t m = mine[w * 32 + lane];
+            if (m) {
+              cnt += __popc(m);
+              atomicOr(&pbm[w], m);
+            }
+          }
+          sv2 += static_cast<double>(cnt) * cnt;
+        }
+      }
+    }
+    __syncwarp();
+    int c = 0;
+    for (int w = lane; w < words; w += 32) c += __popc(pbm[w]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      sp2 += static_cast<double>(c) * c;
+      n_pairs += 1;
+    }
+    __syncwarp();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    n_pix += __shfl_xor_sync(0xffffffffu, n_pix, o);
+    sv2 += __shfl_xor_sync(0xffffffffu, sv2, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&out->pairs, n_pairs);
+    atomicAdd(&out->pix, n_pix);
+    atomicAdd(&out->sv2, sv2);
+    atomicAdd(&out->sp2, sp2);
+  }
+}
 
 }  // namespace
 
@@ -765,6 +921,22 @@ cudaError_t launch_dm_finalize(const double* G, const double* wdm, double* D, do
   const int64_t n = static_cast<int64_t>(nb) * nb * n_mocks;
   if (n == 0) return cudaSuccess;
   LYA_COUNT(1), dm_finalize_kernel<<<grid_for(n, 256), 256, 0, s>>>(G, wdm, D, wdm_out, nb, n_mocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dm_work(const DmArgs& a, const DevInfo& dev, DmWork* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(DmWork), s);
+  if (e != cudaSuccess || a.n_pairs == 0 || a.p_subsample <= 0.0) return e;
+  const int all = a.p_subsample >= 1.0 ? 1 : 0;
+  const uint64_t thr = all ? 0 : static_cast<uint64_t>(a.p_subsample * 18446744073709551616.0);
+  const int words_cap = (a.n_par * a.n_perp + 31) / 32;
+  int warps = 8;
+  while (warps > 1 && warps * 33 * words_cap * 4 > dev.smem_optin) warps >>= 1;
+  const int smem = warps * 33 * words_cap * 4;
+  if (smem > dev.smem_optin) return cudaErrorInvalidValue;
+  e = set_max_dynamic_smem(reinterpret_cast<const void*>(dm_work_kernel), smem);
+  if (e != cudaSuccess) return e;
+  LYA_COUNT(1), dm_work_kernel<<<dev.sms * 4, warps * 32, smem, s>>>(a, thr, all, words_cap, out);
   return cudaGetLastError();
 }
 

@@ -174,6 +174,8 @@ struct XiArgs {
   int nb;
   unsigned long long* counter;
 };
+// largest n_par the mixed pair kernel's shared-memory layout holds
+int xi_mixed_max_npar();
 cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps, int grab,
                           XiLaunch* L);
 cudaError_t launch_xi_mixed(const XiArgs& a, const XiLaunch& L, cudaStream_t s);
@@ -199,11 +201,20 @@ struct DmArgs {
   int max_len;
   int n_mocks;      // catalogues in the batch (forest f belongs to F.mock[f])
   const int32_t* fbase;   // [n_mocks] first forest of each catalogue (set by run_dmat)
+  int tensor_tiles;       // rank-1 tiles: 0 = FP32 FMA, 1 = TF32x3 tensor cores (mma.sync)
 };
 cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t* scratch_cap,
                      cudaStream_t s);
 cudaError_t launch_dm_finalize(const double* G, const double* wdm, double* D, double* wdm_out,
                                int nb, int n_mocks, cudaStream_t s);
+// work counts of the closed form over the kept pairs (single catalogue)
+struct DmWork {
+  unsigned long long pairs;   // kept forest pairs with an in-grid band
+  unsigned long long pix;     // their in-grid pixel pairs
+  double sv2;                 // sum over rank-1 vectors (rows of a, columns of b) of |S_v|^2
+  double sp2;                 // sum over pairs of |S_pair|^2
+};
+cudaError_t launch_dm_work(const DmArgs& a, const DevInfo& dev, DmWork* out, cudaStream_t s);
 
 // adjoint.cu
 struct AdjArgs {
@@ -214,6 +225,7 @@ struct AdjArgs {
   Forests F;
   int n_par, n_perp;
   const double* grad_xi;
+  const double* grad_wsum;   // dL/dW_A (NULL = 0)
   const double* xi;
   const double* wsum;
   const float* delta;   // caller's delta (for dL/dw = delta * ...)
@@ -318,12 +330,14 @@ struct MeansArgs {
   double d_par, d_perp;  // bin widths
   unsigned* err;
   int max_len;
+  const double* zpix;    // per-pixel redshift (single catalogue: packed index = pixel index), or NULL
 };
 size_t means_scratch_bytes(int64_t n_forests, int64_t n_pairs, int nb);
-int means_smem_bytes(int nb, int max_len);
-// outputs: wsum, rpar_mean, rperp_mean, dist_mean [nb] float64 (wsum may be NULL), count [nb] int64
+int means_smem_bytes(int nb, int max_len, bool with_z);
+// outputs: wsum, rpar_mean, rperp_mean, dist_mean [nb] float64 (wsum may be NULL), z_mean [nb] (needs
+// a.zpix; NULL = not computed), count [nb] int64
 cudaError_t launch_bin_means(const MeansArgs& a, const DevInfo& dev, void* scratch, double* wsum, double* rpar_mean,
-                             double* rperp_mean, double* dist_mean, int64_t* count, cudaStream_t s);
+                             double* rperp_mean, double* dist_mean, double* z_mean, int64_t* count, cudaStream_t s);
 
 // scratch helper (api.cu).  While the calling thread captures a CUDA graph
 // (lya_capture_begin) it allocates nothing and fails with

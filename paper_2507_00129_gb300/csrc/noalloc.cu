@@ -7,6 +7,7 @@
 // array's name as a device address (it is a host-side stand-in); the device
 // address is obtained once per device with cudaGetSymbolAddress and cached.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "lya_internal.cuh"
@@ -71,10 +72,13 @@ extern "C" int lya_xi_pairs_static(const lya_catalog* cat, const lya_bins* bins,
   if (cat->n_forests > 0 && (!cat->ra || !cat->dec)) return LYA_ERR_INVALID_ARG;
   if (cat->n_pix > 0 && (!cat->dist || !cat->loglam || !cat->delta || !cat->weight))
     return LYA_ERR_INVALID_ARG;
-  if (bins->n_par < 1 || bins->n_par > 512 || bins->n_perp < 1 || bins->n_perp > 4096 ||
+  // the limits of lya_xi_pairs (MIXED), then the static array's
+  if (bins->n_par < 1 || bins->n_par > xi_mixed_max_npar() || bins->n_perp < 1 || bins->n_perp > 4096 ||
       static_cast<int64_t>(bins->n_par) * bins->n_perp > kStaticBins)
     return LYA_ERR_TOO_LARGE;
-  if (!(bins->r_par_max > 0) || !(bins->r_perp_max > 0)) return LYA_ERR_INVALID_ARG;
+  if (!(bins->r_par_max > 0) || !(bins->r_perp_max > 0) || !std::isfinite(bins->r_par_max) ||
+      !std::isfinite(bins->r_perp_max))
+    return LYA_ERR_INVALID_ARG;
   if (cat->n_forests > kStaticForests || cat->n_pix > kStaticPix || n_pairs > kStaticPairs)
     return LYA_ERR_TOO_LARGE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -605,9 +605,14 @@ __global__ void finalize_kernel(const double* num, const double* wsum, double* x
 
 }  // namespace
 
+int xi_mixed_max_npar() {
+  // two chunk-histogram rows (band row and guard row) of n_par + 1 words below the 32 dummy words
+  return std::min((kHcap - 32) / 2 - 1, kAcap);
+}
+
 cudaError_t plan_xi_mixed(const DevInfo& dev, int n_par, int max_len, int warps, int grab,
                           XiLaunch* L) {
-  if (2 * (n_par + 1) > kHcap - 32 || n_par > kAcap) return cudaErrorInvalidValue;
+  if (n_par > xi_mixed_max_npar()) return cudaErrorInvalidValue;
   int seg = ((std::max(max_len, 1) + 31) / 32) * 32;
   if (seg > kMaxSeg) seg = kMaxSeg;
   // longer forests are staged in segments: shrink the segment until the block fits

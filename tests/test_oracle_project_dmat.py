@@ -185,3 +185,21 @@ def test_dmat_edge_allowance_brackets_shifted_binning(cat0, bins0):
     # the allowance is small where nothing is near an edge: zero without ambiguous pairs
     far = odm.dmat(sub, bins0, pr, eps_edge=1e-12)
     assert far["edge_d"].sum() < 1e-6 * E.sum()
+
+
+def test_closed_form_work_counts_by_hand():
+    """Two forests, all pixel pairs in one bin except one: the column vectors
+    touch {0} and {0, 1}, the rows likewise; the pair touches two bins."""
+    from conftest import line_catalog
+    from oracle import dmat as odm
+    f0 = (0.0, 0.0, [1000.0, 1001.0], [8.2, 8.3], [0.1, 0.2], [1.0, 1.0])
+    f1 = (1e-6, 0.0, [1000.5, 1005.5], [8.2, 8.3], [0.3, -0.2], [1.0, 2.0])
+    cat = line_catalog([f0, f1])
+    bins = synth.Bins(4, 4, 16.0, 16.0)   # 4 Mpc/h bins
+    # |d_i - d_j|: (0.5, 5.5), (0.5, 4.5) -> bins p = (0, 1), (0, 1)
+    w = odm.closed_form_work(cat, bins, (np.array([0]), np.array([1])))
+    assert w["pixel_pairs"] == 4
+    # columns: j=0 -> {p0}, j=1 -> {p1}; rows: i=0 -> {p0, p1}, i=1 -> {p0, p1}
+    assert w["sum_vec_support_sq"] == 1 + 1 + 4 + 4
+    assert w["sum_pair_support_sq"] == 4
+    assert w["flops"] == 20 * 4 + 4 * 10 + 8 * 4
