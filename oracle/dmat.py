@@ -222,3 +222,34 @@ def pair_pairs(cat, bins, pair_list) -> float:
         k = float(np.count_nonzero(ok))
         tot += k * k
     return tot
+
+
+def closed_form_work(cat, bins, pair_list) -> dict:
+    """Work counts of the closed form above, per forest pair of ``pair_list``:
+    the in-grid pixel pairs, the sum over rank-1 vectors (each column j of b,
+    a histogram over i of a, and each row i of a) of |S_v|^2 with |S_v| the
+    number of distinct bins the vector's pixel pairs fall in, and the sum of
+    |S_pair|^2 over pairs with |S_pair| the distinct bins of the pair.  The
+    algorithmic flops of the closed form are about 20 per in-grid pixel pair
+    plus 4 sum |S_v|^2 (two rank-1 outer products per vector) plus
+    8 sum |S_pair|^2 (four T outer products)."""
+    nvec = unit_vectors(cat.ra, cat.dec)
+    pix = 0
+    sv2 = 0.0
+    sp2 = 0.0
+    for a, b in zip(*pair_list):
+        sa, sb = cat.forest(a), cat.forest(b)
+        if sa.stop == sa.start or sb.stop == sb.start:
+            continue
+        c, s = half_angle(nvec[a], nvec[b])
+        A, ok, _, _ = pixel_pair_bins(cat.dist[sa], cat.dist[sb], c, s, bins)
+        if not np.any(ok):
+            continue
+        pix += int(np.count_nonzero(ok))
+        for j in range(A.shape[1]):
+            sv2 += float(len(np.unique(A[ok[:, j], j]))) ** 2
+        for i in range(A.shape[0]):
+            sv2 += float(len(np.unique(A[i, ok[i, :]]))) ** 2
+        sp2 += float(len(np.unique(A[ok]))) ** 2
+    return {"pixel_pairs": pix, "sum_vec_support_sq": sv2, "sum_pair_support_sq": sp2,
+            "flops": 20.0 * pix + 4.0 * sv2 + 8.0 * sp2}
