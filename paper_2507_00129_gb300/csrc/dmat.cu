@@ -43,7 +43,7 @@ namespace lya {
 namespace {
 
 constexpr int kDmThreads = 512;
-constexpr int kChunk = 128;
+constexpr int kChunk = 32;   // pairs per work unit (each pair is flushed on its own; small units balance the SMs)
 
 
 // band of a pair: same FP32 arithmetic as the xi kernel
