@@ -42,10 +42,17 @@ DM_P, DM_SEED = 0.05, 1234
 FLOPS_PER_PAIR = 8  # 4 for the two scaled separations, 2 products, 2 accumulations
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one xi_mixed_kernel launch on the
-# 60,000-forest workload, from one single-pass ncu capture of the full-size launch (summarised in
-# profiles/); keyed by a hash of the kernel's sources and reported only while they are unchanged.
-XI_TRAFFIC = {"sha256": "48247fa6ec1db0575ee3697ff32bbfcf032d47d4aa87439259e8dc94e202a2b7", "bytes": 9421886208 + 13905152}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of xi_mixed_kernel per in-grid pixel pair, from
+# one ncu capture of a smaller catalogue of the same kind (summarised in profiles/), keyed by the workload and a
+# hash of the kernel's sources: a launch's traffic is this times its in-grid pixel pairs, reported only while the
+# sources are unchanged.  Traffic grows with the pairs: every forest pair reads its two forests' pixels (from L2
+# when they are resident) and its pair-list entry.
+XI_TRAFFIC = {
+    # 5.3967 GB read + 17.2 MB written by one launch on a 20,000-forest catalogue of the DESI-Y5-like kind
+    # (5.7033e11 in-grid pixel pairs), profiles/xi_kernel_desi_y5_like_20000.md
+    "desi_y5_like": {"sha256": "36830d8fec5b6442f9f12794cfea873449c57f410633fe94f045dcffc891e2bf",
+                     "bytes_per_pixel_pair": (5396689000 + 17232128) / 570330594405},
+}
 
 
 # FP64 fused multiply-adds per SM per clock measured on this GB300 (a DFMA throughput
@@ -62,10 +69,11 @@ def xi_source_hash() -> str:
     return hsh.hexdigest()
 
 
-def xi_traffic(workload_forests: int):
-    if workload_forests != 60000 or XI_TRAFFIC["sha256"] is None:
+def xi_traffic(workload: str, pixel_pairs: float):
+    t = XI_TRAFFIC.get(workload)
+    if not t or xi_source_hash() != t["sha256"]:
         return None
-    return XI_TRAFFIC["bytes"] if xi_source_hash() == XI_TRAFFIC["sha256"] else None
+    return t["bytes_per_pixel_pair"] * pixel_pairs
 
 
 def peaks():
@@ -312,7 +320,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pixel pairs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD_DESI, impl="CPU FP64 oracle (bounded slice per step)"),
+            "config": dict(WORKLOAD_DESI, **({"forests": args.forests} if args.forests else {}),
+                           impl="CPU FP64 oracle (bounded slice per step)"),
             "cpu_baseline": {"value": v, "unit": "pixel pairs/s", "cores": info["cores"], "kind": "oracle",
                              "cpu_model": info["cpu_model"], "sample": info["sample"]},
             "e2e": {"value": v, "unit": "pixel pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -508,7 +517,7 @@ def sdss_step(args, rank, world, local, steps: int, warmup: int, full: bool = Tr
                        seeds=f"catalogue seed 1+rank, DM seed {DM_SEED}"),
         "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
                      "unit": "TFLOP/s", "frac": ach / peak_fp32,
-                     "traffic": xi_traffic(args.forests or 60000),
+                     "traffic": xi_traffic("sdss_dr16_like", st["pixel_pairs"]),
                      "peak_note": f"FP32 FMA peak {n_sm} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz "
                                   f"(sm_max of {how} peaks); {FLOPS_PER_PAIR} algorithmic flops per "
                                   "in-grid pixel pair; traffic = ncu DRAM bytes of one full-size launch "
@@ -745,7 +754,8 @@ def run_ours(args, rank, world, local):
                        step="project + pair list + xi/W mixed", seeds="catalogue seed 2+rank",
                        fp64_path="plain-FP64 kernel on a seeded 0.5% sample of the forest pairs"),
         "roofline": {"bound": "alu", "kernel": "xi_mixed_kernel", "achieved": ach, "peak": peak_fp32,
-                     "unit": "TFLOP/s", "frac": ach / peak_fp32, "traffic": xi_traffic(spec.n_forests),
+                     "unit": "TFLOP/s", "frac": ach / peak_fp32,
+                     "traffic": xi_traffic("desi_y5_like", st["pixel_pairs"]),
                      "peak_note": f"FP32 FMA peak {n_sm} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz "
                                   f"(sm_max of {how} peaks); {FLOPS_PER_PAIR} algorithmic flops per "
                                   "in-grid pixel pair; achieved over the kernel's own device time (CUDA events "

@@ -129,22 +129,26 @@ __global__ void chunk_fill_kernel(const int32_t* count, const int64_t* start, co
   }
 }
 
-constexpr int kCB = 16;   // vectors per batch
+// vectors per batch: 32 where the band fits in shared memory with them (half
+// the block-wide phases per pair), else 16
+constexpr int kCB = 16;
+constexpr int kCB2 = 32;
 
 // Shared-memory layout of one block (offsets in bytes)
 struct Lay {
   int U, T4, Va, Vb, mark, inv, S, ucs, pixa, pixb, tv, cf, gbin, misc, end;
 };
 
-__host__ __device__ inline int scap_for(int L, int npar, int K) {
-  // union-support capacity: at least one vector's support bound 2 (n_par + K) + 2
+__host__ __device__ inline int scap_for(int L, int npar, int K, int cb) {
+  // union-support capacity: at least one vector's support bound 2 (n_par + K) + 2,
+  // with room for the batch's neighbouring vectors
   int c = 2 * (npar + K) + 2;
-  c = c + c / 2;
+  c = (cb > kCB) ? 2 * c : c + c / 2;
   if (c > L) c = L;
   return (c + 3) & ~3;
 }
 
-// Row stride of the batch vectors V[kCB][.]: at least the support capacity
+// Row stride of the batch vectors V[cb][.]: at least the support capacity
 // rounded up to 16 (the tensor-core tiles read 16-row blocks) and 8 modulo 32,
 // so that the fragment loads of the tensor-core tiles (rows t and t + 4 of a
 // k step, 8 consecutive support entries) hit 32 different banks.
@@ -154,15 +158,15 @@ __host__ __device__ inline int ldv_for(int scap) {
   return v;
 }
 
-__host__ __device__ inline Lay layout(int L, int scap, int max_len, bool global_sink) {
+__host__ __device__ inline Lay layout(int L, int scap, int max_len, bool global_sink, int cb) {
   auto al = [](int v) { return (v + 15) & ~15; };
   Lay y;
   int o = 0;
   y.U = o;
   if (!global_sink) o += al(static_cast<int>((static_cast<int64_t>(L) * (L + 1) / 2) * 4));
   y.T4 = o; o += al(L * 16);
-  y.Va = o; o += al(kCB * ldv_for(scap) * 4);
-  y.Vb = o; o += al(kCB * ldv_for(scap) * 4);
+  y.Va = o; o += al(cb * ldv_for(scap) * 4);
+  y.Vb = o; o += al(cb * ldv_for(scap) * 4);
   y.mark = o; o += al(L);
   y.inv = o; o += al(L * 2);
   y.S = o; o += al(scap * 4);
@@ -328,7 +332,7 @@ __device__ __forceinline__ void dm_tile_store(double* G, float* U, const int32_t
 }
 
 // One forest pair: accumulate its contribution into the triangle (or G).
-template <bool GLOBAL>
+template <bool GLOBAL, int CB>
 __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t0, int K, int L, int scap,
                         unsigned char* sm, const Lay& y) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -416,7 +420,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
     const float inv_scA = reinterpret_cast<float*>(misc)[1];
     const float inv_scB = reinterpret_cast<float*>(misc)[2];
     int v0 = 0;
-    int cb = kCB;
+    int cb = CB;
     while (v0 < nvec) {
       const int cbn = min(cb, nvec - v0);
       // (a1) mark the local bins the batch touches (and reset the slot counter of (b))
@@ -452,7 +456,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
             mark[l] = 0;
           }
         }
-        for (int k = tid; k < kCB * ldv; k += blockDim.x) {
+        for (int k = tid; k < CB * ldv; k += blockDim.x) {
           Va[k] = 0.f;
           Vb[k] = 0.f;
         }
@@ -484,9 +488,9 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
       // rank-1 coefficients sqrt(w_v / W), sqrt(w_v / S).  Item (k, vv) =
       // (bin of S, vector of the batch); the 16 vectors of a bin sit in 16
       // consecutive lanes, which sum the bin's T terms with shuffles.
-      for (int base = 0; base < ns * kCB; base += blockDim.x) {
+      for (int base = 0; base < ns * CB; base += blockDim.x) {
         const int idx = base + tid;
-        const int k = idx / kCB, vv = idx % kCB;
+        const int k = idx / CB, vv = idx % CB;
         const bool act = (k < ns) && (vv < cbn);
         float t1 = 0.f, tx = 0.f, ty = 0.f, txy = 0.f;
         if (act) {
@@ -502,7 +506,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
         }
         if (side == 0) {
 #pragma unroll
-          for (int o = kCB / 2; o > 0; o >>= 1) {
+          for (int o = CB / 2; o > 0; o >>= 1) {
             t1 += __shfl_xor_sync(0xffffffffu, t1, o);
             tx += __shfl_xor_sync(0xffffffffu, tx, o);
             ty += __shfl_xor_sync(0xffffffffu, ty, o);
@@ -537,7 +541,7 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
       }
       __syncthreads();
       v0 += cbn;
-      cb = kCB;
+      cb = CB;
     }
   }
 
@@ -603,18 +607,18 @@ __device__ void dm_pair(const DmArgs& A, double* G, double* wdm, int item, int t
   __syncthreads();
 }
 
-template <bool GLOBAL>
+template <bool GLOBAL, int CB>
 __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk* chunks,
                                                            const int32_t* n_chunks_dev,
                                                            const int32_t* order, const int32_t* wide,
                                                            const int32_t* n_wide_dev, int scap, int Lalloc,
-                                                           unsigned long long* counter) {
+                                                           int kmin, int kmax, unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ long long s_item;
   const int tid = threadIdx.x;
   const int nbins = A.n_par * A.n_perp;
   const int n_items = GLOBAL ? *n_wide_dev : *n_chunks_dev;
-  const Lay y = layout(Lalloc, scap, A.max_len, GLOBAL);
+  const Lay y = layout(Lalloc, scap, A.max_len, GLOBAL, CB);
   float* U = reinterpret_cast<float*>(sm + y.U);
   float4* T4 = reinterpret_cast<float4*>(sm + y.T4);
   unsigned char* mark = sm + y.mark;
@@ -638,6 +642,7 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     int t0, K, first, cnt, mock;
     if (!GLOBAL) {
       const Chunk ch = chunks[item];
+      if (ch.K < kmin || ch.K > kmax) continue;   // another launch's band widths (uniform over the block)
       t0 = ch.t0; K = ch.K; first = ch.begin; cnt = ch.n; mock = ch.mock;
     } else {
       const int pi = wide[item];
@@ -656,7 +661,7 @@ __global__ void __launch_bounds__(kDmThreads, 1) dm_kernel(DmArgs A, const Chunk
     __syncthreads();
     for (int q = 0; q < cnt; ++q) {
       const int pi = GLOBAL ? wide[item] : order[first + q];
-      dm_pair<GLOBAL>(A, G, wdm, pi, t0, K, L, scap, sm, y);
+      dm_pair<GLOBAL, CB>(A, G, wdm, pi, t0, K, L, scap, sm, y);
     }
   }
 }
@@ -818,24 +823,34 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
                      cudaStream_t s) {
   const int nbins = a.n_par * a.n_perp;
   const int max_len = std::max(a.max_len, 1);
-  // largest band that fits in shared memory
-  int kfit = 0, scap = 0;
+  // largest band that fits in shared memory with batches of 16 vectors (kfit)
+  // and with batches of 32 (kfit2 <= kfit)
+  int kfit = 0, scap = 0, kfit2 = 0, scap2 = 0;
   for (int K = a.n_perp; K >= 1; --K) {
     const int L = K * a.n_par;
-    const int sc = scap_for(L, a.n_par, K);
-    if (layout(L, sc, max_len, false).end + 64 <= dev.smem_optin) {
+    const int sc = scap_for(L, a.n_par, K, kCB);
+    if (layout(L, sc, max_len, false, kCB).end + 64 <= dev.smem_optin) {
       kfit = K;
       scap = sc;
       break;
     }
   }
+  for (int K = kfit; K >= 1; --K) {
+    const int L = K * a.n_par;
+    const int sc = scap_for(L, a.n_par, K, kCB2);
+    if (layout(L, sc, max_len, false, kCB2).end + 64 <= dev.smem_optin) {
+      kfit2 = K;
+      scap2 = sc;
+      break;
+    }
+  }
   // wide-pair configuration (triangle in global memory)
   const int Lw = a.n_perp * a.n_par;
-  const int scapw = scap_for(Lw, a.n_par, a.n_perp);
-  if (layout(Lw, scapw, max_len, true).end + 64 > dev.smem_optin) return cudaErrorInvalidValue;
+  const int scapw = scap_for(Lw, a.n_par, a.n_perp, kCB);
+  if (layout(Lw, scapw, max_len, true, kCB).end + 64 > dev.smem_optin) return cudaErrorInvalidValue;
   if (kfit == 0) {  // everything goes wide
     kfit = 1;
-    scap = scap_for(a.n_par, a.n_par, 1);
+    scap = scap_for(a.n_par, a.n_par, 1, kCB);
   }
 
   const int n_mocks = std::max(a.n_mocks, 1);
@@ -894,23 +909,33 @@ cudaError_t run_dmat(const DmArgs& a, const DevInfo& dev, void** scratch, size_t
     LYA_COUNT(1), to_int32_kernel<<<1, 1, 0, s>>>(coff + ngroups, misc + 1);
     LYA_TRY(cudaGetLastError());
   }
-  // main launch: shared-memory triangle
-  {
-    const int L = kfit * a.n_par;
-    const Lay y = layout(L, scap, max_len, false);
-    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<false>), y.end));
+  // shared-memory triangle: bands of up to kfit2 rows with batches of 32
+  // vectors, the wider ones (up to kfit) with batches of 16
+  if (kfit2 > 0) {
+    const int L = kfit2 * a.n_par;
+    const Lay y = layout(L, scap2, max_len, false, kCB2);
+    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<false, kCB2>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<false><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
-                                                                      scap, L, counter);
+    LYA_COUNT(1), dm_kernel<false, kCB2><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide,
+                                                                            misc, scap2, L, 1, kfit2, counter);
+    LYA_TRY(cudaGetLastError());
+  }
+  if (kfit2 < kfit) {
+    const int L = kfit * a.n_par;
+    const Lay y = layout(L, scap, max_len, false, kCB);
+    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<false, kCB>), y.end));
+    LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
+    LYA_COUNT(1), dm_kernel<false, kCB><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
+                                                                           scap, L, kfit2 + 1, kfit, counter);
     LYA_TRY(cudaGetLastError());
   }
   // wide pairs
   {
-    const Lay y = layout(Lw, scapw, max_len, true);
-    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<true>), y.end));
+    const Lay y = layout(Lw, scapw, max_len, true, kCB);
+    LYA_TRY(set_max_dynamic_smem(reinterpret_cast<const void*>(dm_kernel<true, kCB>), y.end));
     LYA_TRY(cudaMemsetAsync(counter, 0, 8, s));
-    LYA_COUNT(1), dm_kernel<true><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
-                                                                     scapw, Lw, counter);
+    LYA_COUNT(1), dm_kernel<true, kCB><<<dev.sms, kDmThreads, y.end, s>>>(a2, chunks, misc + 1, order, wide, misc,
+                                                                          scapw, Lw, 1, a.n_perp, counter);
     LYA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
