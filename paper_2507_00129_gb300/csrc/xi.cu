@@ -12,11 +12,12 @@
 //        r_perp/D =   d~_j *   s/D  + ((d~_i * s/D) + (ref_a + ref_b) s/D)
 //  * floor() is an FP32 add rounded toward -inf of 2^23 (the integer lands in
 //    the low mantissa bits), so the bin index needs no float->int conversion;
-//  * each lane walks j and keeps the current bin's run sums in registers; when
-//    the bin changes the run goes to the warp's chunk histogram, which covers
-//    only the rows of the pair's r_perp band, as exact two-word fixed point
-//    summed with native 32-bit shared-memory reductions (every lane issues
-//    them every step, aimed at its own dummy word when its run goes on);
+//  * each lane walks j and keeps the current bin's run sums in registers; a
+//    run that ends (the bin changed) is held in registers, and the warp adds
+//    the held runs to its chunk histogram, which covers only the rows of the
+//    pair's r_perp band, when a lane that holds one ends another: exact
+//    two-word fixed point summed with native 32-bit shared-memory reductions
+//    (a lane without a held run aims them at its own dummy word);
 //  * every two 32-pixel chunks of forest a the integer sums are folded into a
 //    warp-private compensated FP32 (TwoSum) band accumulator, which survives
 //    across consecutive pairs with the same first band row (the pair list is
@@ -52,13 +53,6 @@ __device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
   hi = s;
 }
 
-// One 32-pixel chunk of forest a against pixels [jlo, jhi) of the staged
-// forest b.  Each lane keeps the current bin and its running sums in
-// registers and adds them to the shared chunk histogram only when the bin
-// changes (a run of consecutive j).  Out-of-grid pairs land in the guard
-// row / column (floor clamped with fminf); WINDOW additionally sends rows
-// outside [twin, twin + tspan] to the guard.
-// One pixel pair of a run walk (see chunk_runs).
 // Exact two-word fixed point.  v (|v| < B) is represented as
 // (hi * 2^16 + lo) * 2^-k with q = v * 2^(k-16), hi = floor(q), lo =
 // round((q - hi) * 2^16) in [0, 2^16]; sc16 = 2^(k-16) is chosen per forest
@@ -75,46 +69,67 @@ __device__ __forceinline__ void split_fixed(float v, float sc16, uint32_t& hi, u
   lo = __float_as_uint(lm) - kM15Bits;
 }
 
-// One pixel pair of a run walk (see chunk_runs).
+// A lane's ended run, held in registers until the warp adds the held runs to
+// the chunk histogram.
+struct Held {
+  uint32_t key;
+  float n, w;
+  bool on;
+};
+
+// Adds every lane's held run to the chunk histogram (four 32-bit reductions
+// per lane; a lane without a held run adds to its own dummy word).
+__device__ __forceinline__ void add_held(Held& h, uint32_t base, float scN, float scW, uint32_t dummy) {
+  uint32_t nh, nl, wh, wl;
+  split_fixed(h.n, scN, nh, nl);
+  split_fixed(h.w, scW, wh, wl);
+  const uint32_t addr = h.on ? base + (h.key << 2) : dummy;
+  asm volatile(
+      "{\n\t"
+      "red.shared.add.u32 [%0], %1;\n\t"
+      "red.shared.add.u32 [%0+%5], %2;\n\t"
+      "red.shared.add.u32 [%0+%6], %3;\n\t"
+      "red.shared.add.u32 [%0+%7], %4;\n\t}"
+      ::"r"(addr), "r"(nh), "r"(nl), "r"(wh), "r"(wl), "n"(kHcap * 4), "n"(kHcap * 8), "n"(kHcap * 12));
+  h.on = false;
+}
+
+// One pixel pair of a run walk (see chunk_runs).  A run that ends here is
+// held in the lane's registers; the warp adds its held runs to the histogram
+// only when some lane that already holds one ends another.  On the DESI-like
+// grid a run is about seven pixels long, so the reductions come once per ~6
+// steps instead of every step.
 template <bool WINDOW>
 __device__ __forceinline__ void run_step(const Pix& q, float cp, float sp, float uc, float us, float wdi,
                                          float wi, float pmax, float tmax, uint32_t stride, uint32_t base,
                                          float scN, float scW, uint32_t guard, uint32_t twin,
-                                         uint32_t tspan, uint32_t dummy, uint32_t& cur, float& aN, float& aW) {
+                                         uint32_t tspan, uint32_t dummy, uint32_t& cur, float& aN, float& aW,
+                                         Held& held) {
   const float rp = fabsf(fmaf(-q.x, cp, uc));
   const float rt = fmaf(q.x, sp, us);
   const float pf = fminf(__fadd_rd(rp, kMagic), pmax);
   const float tf = fminf(__fadd_rd(rt, kMagic), tmax);
   uint32_t key = __float_as_uint(tf) * stride + __float_as_uint(pf);
   if (WINDOW) key = ((__float_as_uint(tf) - kMagicBits - twin) <= tspan) ? key : guard;
-  const uint32_t chg = key != cur ? 1u : 0u;
-  // the run that ends here (if the bin changed) goes to the chunk histogram
-  uint32_t nh, nl, wh, wl;
-  split_fixed(aN, scN, nh, nl);
-  split_fixed(aW, scW, wh, wl);
-  // every lane issues its four reductions on every step (a predicated
-  // shared-memory atomic costs a branch); a lane whose run goes on adds to its
-  // own dummy word, a lane whose run ended adds the run to its bin
-  const uint32_t addr = chg ? base + (cur << 2) : dummy;
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(nh));
-  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(nl), "n"(kHcap * 4));
-  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(wh), "n"(kHcap * 8));
-  asm volatile("red.shared.add.u32 [%0+%2], %1;" ::"r"(addr), "r"(wl), "n"(kHcap * 12));
-  aN = chg ? 0.f : aN;
-  aW = chg ? 0.f : aW;
+  const bool chg = key != cur;
+  if (__any_sync(0xffffffffu, chg && held.on)) add_held(held, base, scN, scW, dummy);
+  held.key = chg ? cur : held.key;
+  held.n = chg ? aN : held.n;
+  held.w = chg ? aW : held.w;
+  held.on = held.on || chg;
   cur = key;
-  aN = fmaf(wdi, q.z, aN);
-  aW = fmaf(wi, q.y, aW);
+  aN = fmaf(wdi, q.z, chg ? 0.f : aN);
+  aW = fmaf(wi, q.y, chg ? 0.f : aW);
 }
 
 // One 32-pixel chunk of forest a against pixels [jlo, jhi) of the staged
 // forest b.  Each lane keeps the current bin and its running sums in
-// registers and adds them to the shared chunk histogram only when the bin
-// changes (a run of consecutive j).  Out-of-grid pairs land in the guard
-// row / column (floor clamped with fminf); WINDOW additionally sends rows
-// outside [twin, twin + tspan] to the guard.  Pixels are read eight at a time
-// before the eight steps: the reductions write shared memory, so a later
-// load cannot be hoisted above them.
+// registers; a run (consecutive j in one bin) that ends is held (see
+// run_step) and later added to the shared chunk histogram.  Out-of-grid pairs
+// land in the guard row / column (floor clamped with fminf); WINDOW
+// additionally sends rows outside [twin, twin + tspan] to the guard.  Pixels
+// are read eight at a time before the eight steps: the reductions write
+// shared memory, so a later load cannot be hoisted above them.
 template <bool WINDOW>
 __device__ __forceinline__ void chunk_runs(const Pix* __restrict__ buf, int jlo, int jhi, float cp,
                                            float sp, float uc, float us, float wdi, float wi,
@@ -123,6 +138,7 @@ __device__ __forceinline__ void chunk_runs(const Pix* __restrict__ buf, int jlo,
                                            uint32_t tspan, uint32_t dummy) {
   uint32_t cur = guard;
   float aN = 0.f, aW = 0.f;
+  Held held{guard, 0.f, 0.f, false};
   int j = jlo;
   for (; j + 8 <= jhi; j += 8) {
     Pix q[8];
@@ -131,23 +147,15 @@ __device__ __forceinline__ void chunk_runs(const Pix* __restrict__ buf, int jlo,
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       run_step<WINDOW>(q[u], cp, sp, uc, us, wdi, wi, pmax, tmax, stride, base, scN, scW, guard, twin, tspan,
-                       dummy, cur, aN, aW);
+                       dummy, cur, aN, aW, held);
   }
   for (; j < jhi; ++j)
     run_step<WINDOW>(buf[j], cp, sp, uc, us, wdi, wi, pmax, tmax, stride, base, scN, scW, guard, twin, tspan,
-                     dummy, cur, aN, aW);
-  // the last run
-  uint32_t nh, nl, wh, wl;
-  split_fixed(aN, scN, nh, nl);
-  split_fixed(aW, scW, wh, wl);
-  const uint32_t addr = base + (cur << 2);
-  asm volatile(
-      "{\n\t"
-      "red.shared.add.u32 [%0], %1;\n\t"
-      "red.shared.add.u32 [%0+%5], %2;\n\t"
-      "red.shared.add.u32 [%0+%6], %3;\n\t"
-      "red.shared.add.u32 [%0+%7], %4;\n\t}"
-      ::"r"(addr), "r"(nh), "r"(nl), "r"(wh), "r"(wl), "n"(kHcap * 4), "n"(kHcap * 8), "n"(kHcap * 12));
+                     dummy, cur, aN, aW, held);
+  // the held runs, then the last run of every lane
+  if (__any_sync(0xffffffffu, held.on)) add_held(held, base, scN, scW, dummy);
+  held = Held{cur, aN, aW, true};
+  add_held(held, base, scN, scW, dummy);
 }
 
 // Per-pair scale sc16 = 2^(20 - e) with 2^e <= B < 2^(e+1): every |v| < B
