@@ -48,10 +48,10 @@ FLOPS_PER_PAIR = 8  # 4 for the two scaled separations, 2 products, 2 accumulati
 # sources are unchanged.  Traffic grows with the pairs: every forest pair reads its two forests' pixels (from L2
 # when they are resident) and its pair-list entry.
 XI_TRAFFIC = {
-    # 5.3967 GB read + 17.2 MB written by one launch on a 20,000-forest catalogue of the DESI-Y5-like kind
+    # 5.3883 GB read + 15.9 MB written by one launch on a 20,000-forest catalogue of the DESI-Y5-like kind
     # (5.7033e11 in-grid pixel pairs), profiles/xi_kernel_desi_y5_like_20000.md
-    "desi_y5_like": {"sha256": "36830d8fec5b6442f9f12794cfea873449c57f410633fe94f045dcffc891e2bf",
-                     "bytes_per_pixel_pair": (5396689000 + 17232128) / 570330594405},
+    "desi_y5_like": {"sha256": "2fd3b5e1b9a72de5422dc0054a2f6a7abd1ec3bbda877a3b632a6c97c59fd24e",
+                     "bytes_per_pixel_pair": (5388336000 + 15879168) / 570330594405},
 }
 
 
