@@ -5,7 +5,8 @@ output, as numbers (and held to the parity bars):
   pairs within eps = 6e-5 bin widths of an edge, which FP32 separations may bin
   either way);
 * xi: max |dxi_A| / max(|xi_A|, sigma_A), raw and net of (E^N_A + |xi_A| E^W_A)
-  / W_A; also the plain relative error over bins with |xi_A| > 10 sigma_A;
+  / (W_A - E^W_A) (xi = N / W: flips move it by (dN - xi dW) / (W + dW)); also
+  the plain relative error over bins with |xi_A| > 10 sigma_A;
 * D:  max |dD_AB| / max_B' |D_AB'|, raw and net of the edge allowance
   (E^D_AB + |D_AB| E^W_A) / (W_A - E^W_A); also the plain relative error over
   entries above 1e-3 of their row's maximum.
@@ -77,7 +78,8 @@ def xi_errors(W, N, X, ref):
     out = {"bins": int(on.sum()),
            "W_raw": float(np.max(dW / Wr)), "W_net": float(np.max(np.maximum(dW - E, 0) / Wr)),
            "xi_raw": float(np.max(dx / scale)),
-           "xi_net": float(np.max(np.maximum(dx - (En + np.abs(xr) * E) / Wr, 0) / scale)),
+           "xi_net": float(np.max(np.maximum(dx - np.divide(En + np.abs(xr) * E, Wr - E, out=np.full_like(Wr, np.inf),
+                                                            where=Wr > E), 0) / scale)),
            "xi_plain_rel_strong_bins": float(np.max(dx[strong] / np.abs(xr[strong]))) if strong.any() else None,
            "strong_bins": int(strong.sum())}
     # the parity bars

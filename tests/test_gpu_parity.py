@@ -4,7 +4,8 @@ Tolerances (from the workload's 1e-6 / 1e-5 bars and the FP32 error bound of
 the mixed path's scaled separations):
 * FP64 path: |dW_A| <= 1e-6 W_A, |dxi_A| <= 1e-5 max(|xi_A|, sigma_A).
 * Mixed path: the same plus the oracle's edge mass for eps = 6e-5 bin units,
-  the bound on the FP32 error of the scaled separations.
+  the bound on the FP32 error of the scaled separations: E^W for W, E^N for
+  N, and for xi = N / W the quotient's (E^N + |xi| E^W) / (W - E^W).
 * D = D~ / W^DM: with |dD~_AB| <= E^D_AB (the oracle's edge_d: what pixel
   pairs within eps of an edge can move into or out of row A or column B) and
   |dW_A| <= E^W_A, D_AB + dD_AB = (D~_AB + dD~_AB) / (W_A + dW_A) gives
@@ -58,6 +59,18 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
+def _xi_allowance(ref):
+    """Mixed-path bound on |dxi_A|: 1e-5 max(|xi_A|, sigma_A), plus what the
+    edge pixel pairs can move.  xi = N / W, so flips that change N by dN and W
+    by dW change xi by (dN - xi dW) / (W + dW); with |dN| <= E^N, |dW| <= E^W
+    that is at most (E^N + |xi| E^W) / (W - E^W), unbounded where every pair
+    of the bin is an edge pair."""
+    den = ref["wsum"] - ref["edge_w"]
+    edge = np.divide(ref["edge_n"] + np.abs(ref["xi"]) * ref["edge_w"], den, out=np.full_like(den, np.inf),
+                     where=den > 0)
+    return 1e-5 * np.maximum(np.abs(ref["xi"]), ref["sigma"]) + edge
+
+
 # ------------------------------------------------------------------ pair list
 def test_pair_list_equals_oracle(api, handle, c0):
     cat, bins, pr = c0
@@ -94,11 +107,47 @@ def test_xi_mixed_matches_oracle_within_edge_allowance(api, handle, c0, ref0):
     assert np.all(dW <= 1e-6 * ref0["wsum"] + ref0["edge_w"] + 1e-9)
     assert np.all(np.abs(N - ref0["num"]) <= 1e-5 * np.sqrt(ref0["num_sq"]) + ref0["edge_n"] + 1e-9)
     on = ref0["wsum"] > 0
-    allow = (1e-5 * np.maximum(np.abs(ref0["xi"]), ref0["sigma"])
-             + (ref0["edge_n"] + np.abs(ref0["xi"]) * ref0["edge_w"]) / np.where(on, ref0["wsum"], 1))
+    allow = _xi_allowance(ref0)
     assert np.all(np.abs(X - ref0["xi"])[on] <= allow[on] + 1e-15)
     # the flips are rare: the total moved weight is far below the allowance
     assert dW.sum() <= 0.05 * ref0["edge_w"].sum() + 1e-6 * ref0["wsum"].sum()
+
+
+def test_xi_wide_bands_in_windows_match_oracle(api, handle, c0):
+    """r_perp bins of 1/3 Mpc/h: a forest pair's r_perp band then spans more rows than the pair kernels hold at
+    once (14 rows of 25 r_par bins in the mixed kernel, 10 in the FP64 one), so they take such pairs in windows
+    of rows, each window a pass over the pair.  Here r_perp / D_perp reaches 300, so three of the FP32 roundings in
+    the scaled r_perp are of values up to 300 (1.5e-5 each) and the rounding of s / D_perp adds 1.8e-5: the bound
+    on its error is ~6.6e-5 bin units, and the edge mass is taken at eps = 1e-4."""
+    cat, _, _ = c0
+    bins = synth.Bins(25, 300, 100.0, 100.0)
+    pr = oracle.pairs.forest_pairs(cat, bins)
+    # band rows of each pair, from its forests' extreme distances (r_perp grows with both distances)
+    from oracle.geometry import unit_vectors
+    nv = unit_vectors(cat.ra, cat.dec)
+    a, b = pr
+    s = 0.5 * np.linalg.norm(nv[a] - nv[b], axis=1) / (bins.r_perp_max / bins.n_perp)
+    lo = np.floor((cat.dist[cat.offsets[a]] + cat.dist[cat.offsets[b]]) * s)
+    hi = np.minimum(np.floor((cat.dist[cat.offsets[a + 1] - 1] + cat.dist[cat.offsets[b + 1] - 1]) * s),
+                    bins.n_perp - 1)
+    rows = (hi - lo + 1)[lo < bins.n_perp]
+    assert np.mean(rows > 14) > 0.5 and np.mean(rows > 10) > 0.7
+    ref = oracle.xi.xi_sums(cat, bins, pr, eps_edge=1e-4, processes=0)
+    dc = api.DeviceCatalog.from_host(cat)
+    on = ref["wsum"] > 0
+    num, wsum, xi = api.lya_xi(handle, dc, bins, "fp64")
+    api.lya_sync_status(handle)
+    W, N, X = _np(wsum), _np(num), _np(xi)
+    assert np.all(np.abs(W - ref["wsum"]) <= 1e-6 * ref["wsum"] + 1e-12)
+    assert np.all(np.abs(X - ref["xi"]) <= 1e-5 * np.maximum(np.abs(ref["xi"]), ref["sigma"]) + 1e-15)
+    num, wsum, xi = api.lya_xi(handle, dc, bins, "mixed")
+    api.lya_sync_status(handle)
+    W, N, X = _np(wsum), _np(num), _np(xi)
+    assert np.all(np.abs(W - ref["wsum"]) <= 1e-6 * ref["wsum"] + ref["edge_w"] + 1e-9)
+    assert np.all(np.abs(N - ref["num"]) <= 1e-5 * np.sqrt(ref["num_sq"]) + ref["edge_n"] + 1e-9)
+    allow = _xi_allowance(ref)
+    assert np.all(np.abs(X - ref["xi"])[on] <= allow[on] + 1e-15)
+    assert np.all(X[~on] == 0)
 
 
 def test_flip_tally_is_bounded_by_edge_mass(api, handle, c0, ref0):

@@ -39,8 +39,11 @@ def _check_against_oracle(cat, bins, a, b, num, wsum, xi):
     assert np.all(np.abs(W - ref["wsum"]) <= 1e-6 * ref["wsum"] + ref["edge_w"] + 1e-9)
     assert np.all(np.abs(N - ref["num"]) <= 1e-5 * np.sqrt(ref["num_sq"]) + ref["edge_n"] + 1e-9)
     on = ref["wsum"] > 0
+    # xi = N / W: edge flips move it by (dN - xi dW) / (W + dW), at most (E^N + |xi| E^W) / (W - E^W)
+    den = ref["wsum"] - ref["edge_w"]
     allow = (1e-5 * np.maximum(np.abs(ref["xi"]), ref["sigma"])
-             + (ref["edge_n"] + np.abs(ref["xi"]) * ref["edge_w"]) / np.where(on, ref["wsum"], 1))
+             + np.divide(ref["edge_n"] + np.abs(ref["xi"]) * ref["edge_w"], den, out=np.full_like(den, np.inf),
+                         where=den > 0))
     assert np.all(np.abs(X - ref["xi"])[on] <= allow[on] + 1e-15)
     assert np.all(X[~on] == 0)
 
